@@ -1,0 +1,36 @@
+"""Writes tests/golden/helmholtz2d_n1024_p4.json from the CPU oracle only.
+
+The paper prints no worked example (its Tables 2-3 need matrices that are not
+available), so the stored values here are the oracle's own recursive residual
+histories on the seeded 32x32 2D Helmholtz problem (Sec. 3 setting: X0 = 0,
+tol 1e-10, stopping rule ||xi_m||_F/||B||_F of Algorithms 2-3).  They serve as a
+regression fixture for the oracle and as stored expected values for the GPU tests.
+
+Run:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle.blcoc_oracle as O                      # noqa: E402
+from paper_1601_05362_gb300 import problems as P      # noqa: E402
+
+
+def main():
+    out = {"source": "oracle/blcoc_oracle.py (Algorithms 2-3, Sec. 2.2)", "problem": None, "runs": {}}
+    for method, f in (("cocg_rq", O.bl_cocg_rq), ("cocr_rq", O.bl_cocr_rq)):
+        pr = P.helmholtz2d_n1024_p4(method)
+        A = pr.A.to_scipy()
+        r = f(A, pr.B, tol=pr.tol, maxit=pr.maxit)
+        out["problem"] = pr.name
+        out["runs"][method] = {"status": r.status, "iters": r.iters, "hist": r.hist,
+                               "trr": O.true_relres(A, pr.B, r.X)}
+    with open(os.path.join(HERE, "helmholtz2d_n1024_p4.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()
