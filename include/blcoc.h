@@ -1,0 +1,156 @@
+/*
+ * blcoc.h - C ABI of libblcoc.so: block COCG / block COCR with residual
+ * orthonormalization for complex symmetric sparse systems, on one GB300 GPU.
+ *
+ * Problem (Sec. 1, Eq. 1.1): A X = B with A in C^{n x n} complex symmetric
+ * (A = A^T, A != A^H), sparse; X, B in C^{n x p}, p << n.
+ *
+ * Methods: bl_cocg_rq (Algorithm 2, Sec. 2.2) and bl_cocr_rq (Algorithm 3, Sec. 2.2).
+ * Every coefficient uses the unconjugated bilinear form Y^T Z (Table 1); only the
+ * thin QR of the residual block is orthonormal in the Hermitian sense, Q^H Q = I_p.
+ * The QR is computed as a Cholesky QR: tau^H tau = W^H W with tau upper triangular
+ * and a real positive diagonal, Q = W tau^{-1} (same factor as a Householder QR whose
+ * diagonal is normalised to be real and positive).
+ *
+ * Data layout
+ *   - complex numbers are interleaved (re, im) doubles (C99 double _Complex,
+ *     numpy complex128, torch.complex128);
+ *   - an n x p block is row-major with row stride p: element (i, j) at offset i*p + j;
+ *   - A is CSR with both triangles stored: int32 row_ptr[n+1] (row_ptr[0] = 0,
+ *     non-decreasing, row_ptr[n] = nnz < 2^31), int32 col_idx[nnz] strictly
+ *     increasing within each row, values vals[nnz].
+ *
+ * Threading: a handle is not thread safe; use one handle per host thread.
+ * Errors: every entry point returns a blcoc_status; nothing throws across the ABI.
+ * blcoc_last_error() gives a one-line description of the last failure on a handle.
+ */
+#ifndef BLCOC_H
+#define BLCOC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct blcoc_ctx* blcoc_handle;
+
+typedef enum {
+  BLCOC_OK = 0,
+  BLCOC_ERR_INVALID_ARG = 1,   /* a size, pointer, method or tolerance is out of range  */
+  BLCOC_ERR_NOT_SYMMETRIC = 2, /* create: pattern or values of A are not symmetric       */
+  BLCOC_ERR_CUDA = 3,          /* a CUDA runtime call failed (see blcoc_last_error)      */
+  BLCOC_ERR_OOM = 4,           /* device allocation failed                               */
+  BLCOC_NOT_CONVERGED = 5,     /* maxit iterations ran without reaching tol              */
+  BLCOC_BREAKDOWN = 6,         /* the residual block lost rank, a p x p system was
+                                  singular, or a coefficient became non-finite          */
+  BLCOC_ERR_TIMEOUT = 7        /* reserved: a device wait gave up                        */
+} blcoc_status;
+
+typedef enum { BLCOC_COCG_RQ = 0, BLCOC_COCR_RQ = 1 } blcoc_method;
+
+/* Largest number of right-hand sides one solve accepts. */
+#define BLCOC_MAX_P 32
+
+/*
+ * blcoc_create - upload A and check it.
+ *   out       : receives the handle (set to NULL on failure).
+ *   n, nnz    : order and number of stored entries, 1 <= n, 1 <= nnz < 2^31.
+ *   row_ptr, col_idx, vals : CSR arrays as described above; vals holds 2*nnz doubles.
+ *   host_ptrs : 1 if the three arrays are host memory, 0 if device memory.
+ *   cuda_stream : a cudaStream_t (NULL = legacy default stream). Every solve first
+ *               waits for the work already queued on it; the library runs its own
+ *               kernels on an internal stream of the same device.
+ * The arrays are deep-copied to the device; the caller keeps ownership of them.
+ * Checks (on the GPU): row_ptr monotone, 0 <= col_idx < n, strictly increasing within
+ * rows, and for every stored a_ij a stored a_ji with |a_ij - a_ji| <= 1e-12 max(|a_ij|,
+ * |a_ji|) (Sec. 1: A = A^T).  Failure: BLCOC_ERR_INVALID_ARG or BLCOC_ERR_NOT_SYMMETRIC.
+ * The device is the current CUDA device of the calling thread.
+ */
+blcoc_status blcoc_create(blcoc_handle* out, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                          const int32_t* col_idx, const void* vals, int host_ptrs, void* cuda_stream);
+
+/*
+ * blcoc_solve - run Algorithm 2 (BLCOC_COCG_RQ) or Algorithm 3 (BLCOC_COCR_RQ).
+ *   B     : n x p right-hand sides (read only).
+ *   X     : n x p, on entry the initial guess X_0, on exit the last iterate.
+ *   p     : 1 <= p <= BLCOC_MAX_P.
+ *   tol   : stop at the top of iteration m when ||xi_m||_F / ||B||_F <= tol
+ *           (Algorithms 2-3, line 3); tol >= 0 (tol = 0 runs exactly maxit iterations).
+ *   maxit : maximum number of iterations, maxit >= 0.
+ * B and X may be device pointers or host pointers (pageable or pinned); host data is
+ * copied through handle-owned device buffers.  B must not alias X.
+ * Workspace (about 6 n x p blocks) is owned by the handle and grows to the largest p
+ * used.  The call blocks until the solve ends.
+ * On return the caller's stream (given at create) is ordered after the solve's work.
+ * Returns BLCOC_OK (converged), BLCOC_NOT_CONVERGED, BLCOC_BREAKDOWN (X then holds
+ * the last complete iterate), or an error code.  ||B||_F = 0 returns X = 0, OK.
+ */
+blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_method method, double tol,
+                         int maxit);
+
+/*
+ * blcoc_get_info - results of the last solve.
+ *   iters            : number of iterations taken (the iterate X holds is X_iters).
+ *   relres_recursive : ||xi_iters||_F / ||B||_F.
+ *   relres_true      : ||B - A X||_F / ||B||_F recomputed from the returned X (Sec. 3,
+ *                      "TRR" before the log10).
+ *   hist, hist_len   : if hist != NULL, receives min(hist_len, iters + 1) values
+ *                      hist[m] = ||xi_m||_F / ||B||_F.
+ * Any output pointer may be NULL.
+ */
+blcoc_status blcoc_get_info(blcoc_handle h, int* iters, double* relres_recursive, double* relres_true,
+                            double* hist, int hist_len);
+
+/*
+ * blcoc_get_xi - the p x p factor xi_iters of the last solve (R = Q xi, Sec. 2.2),
+ * row-major, 2*p*p doubles, written to host memory.
+ */
+blcoc_status blcoc_get_xi(blcoc_handle h, double* xi_out);
+
+/*
+ * blcoc_spmm - Y = A X for an n x p block (the A V product of Algorithms 2-3).
+ * X, Y are device pointers, 1 <= p <= BLCOC_MAX_P, Y must not alias X.  Runs on the
+ * handle's stream order (waits for the creation stream, returns after completion).
+ */
+blcoc_status blcoc_spmm(blcoc_handle h, const void* X, void* Y, int p);
+
+/*
+ * blcoc_residual_norm - ||B - A X||_F for n x p device blocks B, X (Sec. 3's true
+ * residual).  The result is written to *out (host).  Uses handle-owned workspace.
+ */
+blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, int p, double* out);
+
+/*
+ * blcoc_set_option - tuning switches (key, value):
+ *   "graph"      : 1 (default) replays the iteration as a CUDA graph, 0 launches kernels.
+ *   "poll"       : iterations between two host checks of the convergence flag (default 16).
+ *   "timing"     : 1 brackets every row-pass kernel of the iterations with CUDA events on
+ *                  the internal stream (also inside the graph) and accumulates per-kernel
+ *                  device time; 0 (default) records nothing.
+ * Returns BLCOC_ERR_INVALID_ARG for an unknown key or value.
+ */
+blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
+
+/* blcoc_get_stat - counters of the last solve: "launches" (kernels launched by the
+ * solve, including those inside graph replays), "graph_replays", and with the
+ * "timing" option "kt_ns.<kernel>" (total device nanoseconds) and "kt_n.<kernel>"
+ * (launches that did work) for <kernel> in resid, spmm_gram, spmm_plain, cocr_passA,
+ * cocr_passC, cocg_pass1, cocg_pass2. */
+blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value);
+
+/* blcoc_destroy - free the handle and everything it owns.  NULL is accepted. */
+blcoc_status blcoc_destroy(blcoc_handle h);
+
+/* blcoc_status_string - static name of a status code. */
+const char* blcoc_status_string(blcoc_status s);
+
+/* blcoc_last_error - one-line description of the last failure on h ("" if none);
+ * valid until the next call on h.  h = NULL gives the last create failure. */
+const char* blcoc_last_error(blcoc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLCOC_H */

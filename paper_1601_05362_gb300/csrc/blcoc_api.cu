@@ -1,0 +1,701 @@
+// C ABI of libblcoc.so and the host-side solve driver (see include/blcoc.h).
+//
+// One solve = a setup sequence (residual, QR, first products) followed by batches of
+// iterations queued on an internal stream, optionally replayed as a CUDA graph.  The
+// host never waits inside an iteration: the convergence test, the iteration limit and
+// breakdown are decided on the device (control block), every kernel of an iteration
+// returns at once after the decision, and the host reads the control block once per
+// batch of `poll` iterations.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/blcoc.h"
+#include "blcoc_common.cuh"
+#include "blcoc_small.h"
+
+using namespace blcoc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const KernelSet* kernels_for(int p, int* PP) {
+  if (p <= 1) { *PP = 1; return &kernel_set<1>(); }
+  if (p <= 2) { *PP = 2; return &kernel_set<2>(); }
+  if (p <= 4) { *PP = 4; return &kernel_set<4>(); }
+  if (p <= 8) { *PP = 8; return &kernel_set<8>(); }
+  if (p <= 16) { *PP = 16; return &kernel_set<16>(); }
+  *PP = 32;
+  return &kernel_set<32>();
+}
+
+// Names of the timed kernel kinds (index = PassKind of blcoc_rowpass.cuh).
+const char* const kKindNames[] = {"resid", "spmm_gram", "spmm_plain", "cocr_passA", "cocr_passC", "cocg_pass1",
+                                  "cocg_pass2"};
+constexpr int kNumKinds = 7;
+
+struct Timer {
+  int kind;
+  int iter;   // iteration index within the batch
+  cudaEvent_t e0, e1;
+};
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  int p = -1, method = -1, batch = 0, timing = 0;
+  const void* X = nullptr;
+  int64_t gen = -1;
+  int launches = 0;
+  std::vector<Timer> timers;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    p = -1;
+    timers.clear();
+  }
+};
+
+}  // namespace
+
+struct blcoc_ctx {
+  int dev = 0;
+  int num_sms = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  int64_t n = 0, nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  double2* va = nullptr;
+  // workspace
+  int p_cap = 0;
+  int64_t gen = 0;
+  double2 *W = nullptr, *S = nullptr, *U = nullptr, *V = nullptr, *Bst = nullptr, *Xst = nullptr;
+  double2* mats = nullptr;
+  double2* partials = nullptr;
+  size_t partials_cap = 0;   // double2 entries
+  double* stage1 = nullptr;
+  size_t stage1_cap = 0;     // doubles
+  double* hist = nullptr;
+  int hist_cap = 0;
+  Ctrl* ctrl = nullptr;
+  Ctrl* h_ctrl = nullptr;    // pinned
+  int* flags = nullptr;
+  // options
+  int use_graph = 1;
+  int poll = 16;
+  int timing = 0;
+  Graph graph;
+  // kernel timing: event pool and per-kind totals of the last solve
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
+  double kt_ms[kNumKinds] = {0};
+  int64_t kt_n[kNumKinds] = {0};
+  // results of the last solve
+  int last_p = 0;
+  int iters = 0;
+  double relres = 0.0, trr = 0.0;
+  std::vector<double> hist_h;
+  std::vector<double> xi_h;
+  int64_t stat_launches = 0, stat_replays = 0;
+  std::string err;
+};
+
+namespace {
+
+blcoc_status cuda_fail(blcoc_ctx* h, cudaError_t e, const char* what) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return e == cudaErrorMemoryAllocation ? BLCOC_ERR_OOM : BLCOC_ERR_CUDA;
+}
+
+#define CK(h, call)                                             \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+  } while (0)
+
+blcoc_status invalid(blcoc_ctx* h, const char* msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return BLCOC_ERR_INVALID_ARG;
+}
+
+// Partial entries per CTA for any pass: max over kinds (resid: 2 triangles + norms).
+int max_ne(int p) { return 2 * tri_count(p) + 1; }
+
+void free_ws(blcoc_ctx* h) {
+  double2* blocks[] = {h->W, h->S, h->U, h->V, h->Bst, h->Xst, h->mats, h->partials};
+  for (double2* b : blocks)
+    if (b) cudaFree(b);
+  if (h->stage1) cudaFree(h->stage1);
+  h->W = h->S = h->U = h->V = h->Bst = h->Xst = h->mats = h->partials = nullptr;
+  h->stage1 = nullptr;
+  h->p_cap = 0;
+  h->partials_cap = h->stage1_cap = 0;
+}
+
+blcoc_status ensure_ws(blcoc_ctx* h, int p) {
+  if (p <= h->p_cap) return BLCOC_OK;
+  h->graph.reset();
+  free_ws(h);
+  const size_t blk = (size_t)h->n * p * sizeof(double2);
+  CK(h, cudaMalloc(&h->W, blk));
+  CK(h, cudaMalloc(&h->S, blk));
+  CK(h, cudaMalloc(&h->U, blk));
+  CK(h, cudaMalloc(&h->V, blk));
+  CK(h, cudaMalloc(&h->mats, (size_t)M_NSLOTS * PMAX * PMAX * sizeof(double2)));
+  CK(h, cudaMemset(h->mats, 0, (size_t)M_NSLOTS * PMAX * PMAX * sizeof(double2)));
+  const int ne = max_ne(PMAX);
+  h->partials_cap = (size_t)h->num_sms * 4 * ne;
+  CK(h, cudaMalloc(&h->partials, h->partials_cap * sizeof(double2)));
+  h->stage1_cap = (size_t)RED_SPLIT * 2 * ne;
+  CK(h, cudaMalloc(&h->stage1, h->stage1_cap * sizeof(double)));
+  h->p_cap = p;
+  h->gen++;
+  return BLCOC_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ driver
+namespace {
+
+struct Solver {
+  blcoc_ctx* h;
+  const KernelSet* K;
+  int PP, p, method;
+  const double2* B;
+  double2* X;
+  PassArgs base() const {
+    PassArgs a{};
+    a.A = CsrDev{h->n, h->nnz, h->rp, h->ci, h->va};
+    a.p = p;
+    a.W = h->W;
+    a.S = h->S;
+    a.U = h->U;
+    a.V = h->V;
+    a.X = X;
+    a.B = B;
+    a.mats = h->mats;
+    a.partials = h->partials;
+    a.ctrl = h->ctrl;
+    return a;
+  }
+  int launches = 0;
+  std::vector<Timer>* timers = nullptr;   // when set, each pass kernel is bracketed by events
+  int batch_iter = 0;
+  bool capturing = false;                 // events inside a graph must be external record nodes
+  void record(cudaEvent_t e) {
+    if (capturing) cudaEventRecordWithFlags(e, h->s, cudaEventRecordExternal);
+    else cudaEventRecord(e, h->s);
+  }
+  cudaEvent_t next_event() {
+    if (h->evnext == h->evpool.size()) {
+      cudaEvent_t e = nullptr;
+      cudaEventCreate(&e);
+      h->evpool.push_back(e);
+    }
+    return h->evpool[h->evnext++];
+  }
+  void pass(LaunchFn f, int kind, int ne, int flag, double2* in = nullptr) {
+    PassArgs a = base();
+    if (in) a.W = in;   // spmm_gram gathers a.W
+    a.ne = ne;
+    a.flag = flag;
+    a.grid = K->grid(h->n, kind, h->num_sms);
+    Timer t{kind, batch_iter, nullptr, nullptr};
+    if (timers) {
+      t.e0 = next_event();
+      t.e1 = next_event();
+      record(t.e0);
+    }
+    f(a, h->s);
+    if (timers) {
+      record(t.e1);
+      timers->push_back(t);
+    }
+    ++launches;
+    last_grid = a.grid;
+  }
+  int last_grid = 0;
+  void reduce(int ne, const Ctrl* ctrl) {
+    launch_reduce(h->partials, last_grid, ne, h->stage1, ctrl, h->s);
+    ++launches;
+  }
+  void small(SmallKind k, int ne) {
+    launch_small(k, p, method, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s);
+    ++launches;
+  }
+  // kinds must match PassKind in blcoc_rowpass.cuh
+  enum { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2 };
+
+  void setup_residual() {
+    const int E = tri_count(p);
+    pass(K->resid, K_RESID, 2 * E + 1, method == BLCOC_COCG_RQ ? 2 : 0);
+    reduce(2 * E + 1, h->ctrl);
+    small(SK_SETUP, 2 * E + 1);
+  }
+  void setup_rest() {
+    const int E = tri_count(p);
+    if (method == BLCOC_COCR_RQ) {
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 1);   // V_0 = A Q_0, gram W^T A W
+      reduce(E, h->ctrl);
+      small(SK_COCR_H0, E);
+      pass(K->cocr_passC, K_COCR_C, E, 1);     // S_0 = Q_0, U_0 = V_0, gram U^T U
+      reduce(E, h->ctrl);
+    } else {
+      pass(K->cocg_pass2, K_COCG_2, 0, 1);     // S_0 = Q_0
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, h->S);   // A S_0, gram S^T A S
+      reduce(E, h->ctrl);
+    }
+  }
+  void iteration() {
+    const int E = tri_count(p);
+    if (method == BLCOC_COCR_RQ) {
+      small(SK_ALPHA, E);
+      pass(K->cocr_passA, K_COCR_A, E, 0);
+      reduce(E, h->ctrl);
+      small(SK_CHOL, E);
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 1);
+      reduce(E, h->ctrl);
+      small(SK_COCR_BETA, E);
+      pass(K->cocr_passC, K_COCR_C, E, 0);
+      reduce(E, h->ctrl);
+    } else {
+      small(SK_ALPHA, E);
+      pass(K->cocg_pass1, K_COCG_1, 2 * E, 0);
+      reduce(2 * E, h->ctrl);
+      small(SK_CHOL, 2 * E);
+      pass(K->cocg_pass2, K_COCG_2, 0, 0);
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, h->S);   // A S_{m+1}, gram S^T A S
+      reduce(E, h->ctrl);
+    }
+  }
+  void true_residual() {
+    const int E = tri_count(p);
+    PassArgs a = base();
+    a.ne = 2 * E + 1;
+    a.flag = 1 | 16;   // norm only, run after the solve finished
+    a.grid = K->grid(h->n, K_RESID, h->num_sms);
+    K->resid(a, h->s);
+    ++launches;
+    launch_reduce(h->partials, a.grid, 2 * E + 1, h->stage1, nullptr, h->s);
+    ++launches;
+    launch_small(SK_TRR, p, method, h->stage1, 2 * E + 1, h->mats, h->ctrl, h->hist, h->s);
+    ++launches;
+  }
+};
+
+bool is_host_ptr(const void* ptr) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* blcoc_status_string(blcoc_status s) {
+  switch (s) {
+    case BLCOC_OK: return "BLCOC_OK";
+    case BLCOC_ERR_INVALID_ARG: return "BLCOC_ERR_INVALID_ARG";
+    case BLCOC_ERR_NOT_SYMMETRIC: return "BLCOC_ERR_NOT_SYMMETRIC";
+    case BLCOC_ERR_CUDA: return "BLCOC_ERR_CUDA";
+    case BLCOC_ERR_OOM: return "BLCOC_ERR_OOM";
+    case BLCOC_NOT_CONVERGED: return "BLCOC_NOT_CONVERGED";
+    case BLCOC_BREAKDOWN: return "BLCOC_BREAKDOWN";
+    case BLCOC_ERR_TIMEOUT: return "BLCOC_ERR_TIMEOUT";
+  }
+  return "BLCOC_UNKNOWN";
+}
+
+const char* blcoc_last_error(blcoc_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+blcoc_status blcoc_destroy(blcoc_handle h) {
+  if (!h) return BLCOC_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->dev);
+  if (h->s) cudaStreamSynchronize(h->s);
+  h->graph.reset();
+  free_ws(h);
+  if (h->Bst) cudaFree(h->Bst);
+  if (h->Xst) cudaFree(h->Xst);
+  if (h->rp) cudaFree(h->rp);
+  if (h->ci) cudaFree(h->ci);
+  if (h->va) cudaFree(h->va);
+  if (h->hist) cudaFree(h->hist);
+  if (h->ctrl) cudaFree(h->ctrl);
+  if (h->flags) cudaFree(h->flags);
+  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
+  if (h->ev) cudaEventDestroy(h->ev);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+  cudaSetDevice(cur);
+  return BLCOC_OK;
+}
+
+blcoc_status blcoc_create(blcoc_handle* out, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                          const void* vals, int host_ptrs, void* cuda_stream) {
+  if (!out) return invalid(nullptr, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || nnz < 1 || nnz >= (int64_t)1 << 31 || n >= (int64_t)1 << 31)
+    return invalid(nullptr, "n and nnz must satisfy 1 <= n, nnz < 2^31");
+  if (!row_ptr || !col_idx || !vals) return invalid(nullptr, "CSR pointer is NULL");
+  blcoc_ctx* h = new blcoc_ctx();
+  blcoc_status st = BLCOC_OK;
+  auto fail = [&](blcoc_status s) {
+    if (s != BLCOC_OK) {
+      g_create_error = h->err;
+      blcoc_destroy(h);
+    }
+    return s;
+  };
+#define CKC(call)                                                   \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return fail(cuda_fail(h, e_, #call));    \
+  } while (0)
+  CKC(cudaGetDevice(&h->dev));
+  CKC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev));
+  h->user_stream = (cudaStream_t)cuda_stream;
+  h->n = n;
+  h->nnz = nnz;
+  CKC(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  CKC(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+  CKC(cudaMalloc(&h->rp, (n + 1) * sizeof(int)));
+  CKC(cudaMalloc(&h->ci, nnz * sizeof(int)));
+  CKC(cudaMalloc(&h->va, nnz * sizeof(double2)));
+  CKC(cudaMalloc(&h->ctrl, sizeof(Ctrl)));
+  CKC(cudaMalloc(&h->flags, 4 * sizeof(int)));
+  CKC(cudaMallocHost(&h->h_ctrl, sizeof(Ctrl)));
+  const cudaMemcpyKind kind = host_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CKC(cudaEventRecord(h->ev, h->user_stream));
+  CKC(cudaStreamWaitEvent(h->s, h->ev, 0));
+  CKC(cudaMemcpyAsync(h->rp, row_ptr, (n + 1) * sizeof(int), kind, h->s));
+  CKC(cudaMemcpyAsync(h->ci, col_idx, nnz * sizeof(int), kind, h->s));
+  CKC(cudaMemcpyAsync(h->va, vals, nnz * sizeof(double2), kind, h->s));
+  CKC(cudaMemsetAsync(h->flags, 0, 4 * sizeof(int), h->s));
+  launch_validate(n, nnz, h->rp, h->ci, h->va, h->flags, 0, h->s);
+  CKC(cudaGetLastError());
+  int hf[4] = {0, 0, 0, 0};
+  CKC(cudaMemcpyAsync(hf, h->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CKC(cudaStreamSynchronize(h->s));
+  if (hf[0] != 0) {
+    h->err = "CSR structure invalid: row_ptr must start at 0, be non-decreasing and end at nnz; col_idx must be in "
+             "[0,n) and strictly increasing within each row";
+    return fail(BLCOC_ERR_INVALID_ARG);
+  }
+  launch_validate(n, nnz, h->rp, h->ci, h->va, h->flags, 1, h->s);
+  CKC(cudaGetLastError());
+  CKC(cudaMemcpyAsync(hf, h->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CKC(cudaStreamSynchronize(h->s));
+  if (hf[1] != 0) {
+    h->err = "A is not symmetric: some a_ij has no a_ji or |a_ij - a_ji| > 1e-12 max(|a_ij|, |a_ji|)";
+    return fail(BLCOC_ERR_NOT_SYMMETRIC);
+  }
+  prepare_small_kernels();
+  (void)st;
+#undef CKC
+  *out = h;
+  return BLCOC_OK;
+}
+
+blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
+  if (!h || !key) return invalid(h, "NULL handle or key");
+  if (!strcmp(key, "graph")) {
+    if (value != 0 && value != 1) return invalid(h, "graph must be 0 or 1");
+    h->use_graph = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "timing")) {
+    if (value != 0 && value != 1) return invalid(h, "timing must be 0 or 1");
+    if (h->timing != (int)value) h->graph.reset();
+    h->timing = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "poll")) {
+    if (value < 1 || value > 4096) return invalid(h, "poll must be in [1, 4096]");
+    if (h->poll != (int)value) h->graph.reset();
+    h->poll = (int)value;
+    return BLCOC_OK;
+  }
+  return invalid(h, "unknown option");
+}
+
+blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value) {
+  if (!h || !key || !value) return invalid(h, "NULL argument");
+  if (!strcmp(key, "launches")) { *value = h->stat_launches; return BLCOC_OK; }
+  if (!strcmp(key, "graph_replays")) { *value = h->stat_replays; return BLCOC_OK; }
+  for (int k = 0; k < kNumKinds; ++k) {
+    const std::string nm(kKindNames[k]);
+    if (("kt_ns." + nm) == key) { *value = (int64_t)(h->kt_ms[k] * 1e6); return BLCOC_OK; }
+    if (("kt_n." + nm) == key) { *value = h->kt_n[k]; return BLCOC_OK; }
+  }
+  return invalid(h, "unknown stat");
+}
+
+blcoc_status blcoc_spmm(blcoc_handle h, const void* X, void* Y, int p) {
+  if (!h) return invalid(h, "NULL handle");
+  if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
+  if (!X || !Y || X == Y) return invalid(h, "X, Y must be distinct non-NULL device pointers");
+  CK(h, cudaSetDevice(h->dev));
+  int PP = 0;
+  const KernelSet* K = kernels_for(p, &PP);
+  K->prepare();
+  PassArgs a{};
+  a.A = CsrDev{h->n, h->nnz, h->rp, h->ci, h->va};
+  a.p = p;
+  a.W = (double2*)X;
+  a.V = (double2*)Y;
+  a.ctrl = h->ctrl;
+  a.flag = 16;
+  a.grid = K->grid(h->n, 2, h->num_sms);
+  CK(h, cudaEventRecord(h->ev, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
+  K->spmm_plain(a, h->s);
+  CK(h, cudaGetLastError());
+  CK(h, cudaStreamSynchronize(h->s));
+  return BLCOC_OK;
+}
+
+blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, int p, double* out) {
+  if (!h) return invalid(h, "NULL handle");
+  if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
+  if (!B || !X || !out) return invalid(h, "NULL pointer");
+  CK(h, cudaSetDevice(h->dev));
+  blcoc_status st = ensure_ws(h, p);
+  if (st != BLCOC_OK) return st;
+  int PP = 0;
+  Solver sv{h, kernels_for(p, &PP), PP, p, BLCOC_COCR_RQ, (const double2*)B, (double2*)X};
+  sv.K->prepare();
+  CK(h, cudaEventRecord(h->ev, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
+  sv.true_residual();
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+  CK(h, cudaStreamSynchronize(h->s));
+  *out = h->h_ctrl->trr;
+  return BLCOC_OK;
+}
+
+blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_method method, double tol, int maxit) {
+  if (!h) return invalid(h, "NULL handle");
+  h->err.clear();
+  if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
+  if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ) return invalid(h, "unknown method");
+  if (!(tol >= 0.0) || std::isinf(tol)) return invalid(h, "tol must be finite and >= 0");
+  if (maxit < 0) return invalid(h, "maxit must be >= 0");
+  if (!B || !X || B == X) return invalid(h, "B and X must be distinct non-NULL pointers");
+  CK(h, cudaSetDevice(h->dev));
+  blcoc_status st = ensure_ws(h, p);
+  if (st != BLCOC_OK) return st;
+  if (h->hist_cap < maxit + 1) {
+    if (h->hist) cudaFree(h->hist);
+    h->hist = nullptr;
+    h->hist_cap = 0;
+    CK(h, cudaMalloc(&h->hist, (size_t)(maxit + 1) * sizeof(double)));
+    h->hist_cap = maxit + 1;
+  }
+  const size_t bytes = (size_t)h->n * p * sizeof(double2);
+  const bool hostB = is_host_ptr(B), hostX = is_host_ptr(X);
+  if ((hostB || hostX) && (!h->Bst || h->last_p < p)) {
+    if (h->Bst) cudaFree(h->Bst);
+    if (h->Xst) cudaFree(h->Xst);
+    h->Bst = h->Xst = nullptr;
+    CK(h, cudaMalloc(&h->Bst, (size_t)h->n * h->p_cap * sizeof(double2)));
+    CK(h, cudaMalloc(&h->Xst, (size_t)h->n * h->p_cap * sizeof(double2)));
+  }
+  h->last_p = p > h->last_p ? p : h->last_p;
+  CK(h, cudaEventRecord(h->ev, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
+  const double2* dB = (const double2*)B;
+  double2* dX = (double2*)X;
+  if (hostB) {
+    CK(h, cudaMemcpyAsync(h->Bst, B, bytes, cudaMemcpyHostToDevice, h->s));
+    dB = h->Bst;
+  }
+  if (hostX) {
+    CK(h, cudaMemcpyAsync(h->Xst, X, bytes, cudaMemcpyHostToDevice, h->s));
+    dX = h->Xst;
+  }
+  int PP = 0;
+  Solver sv{h, kernels_for(p, &PP), PP, p, (int)method, dB, dX};
+  sv.K->prepare();
+  Ctrl c0{};
+  c0.maxit = maxit;
+  c0.tol = tol;
+  CK(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->s));
+  sv.setup_residual();
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+  CK(h, cudaStreamSynchronize(h->s));
+  h->stat_replays = 0;
+  for (int k = 0; k < kNumKinds; ++k) {
+    h->kt_ms[k] = 0.0;
+    h->kt_n[k] = 0;
+  }
+  bool zero_rhs = false;
+  if (h->h_ctrl->done == 1 && h->h_ctrl->sumsq_b == 0.0) {
+    zero_rhs = true;
+    CK(h, cudaMemsetAsync(dX, 0, bytes, h->s));
+  } else if (!h->h_ctrl->done) {
+    sv.setup_rest();
+    CK(h, cudaGetLastError());
+    const int batch = h->poll;
+    bool use_graph = h->use_graph != 0;
+    std::vector<Timer> direct_timers;
+    if (use_graph) {
+      Graph& g = h->graph;
+      if (!(g.exec && g.p == p && g.method == (int)method && g.batch == batch && g.X == dX && g.gen == h->gen &&
+            g.timing == h->timing)) {
+        g.reset();
+        h->evnext = 0;
+        cudaGraph_t graph = nullptr;
+        CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+        const int before = sv.launches;
+        sv.timers = h->timing ? &g.timers : nullptr;
+        sv.capturing = true;
+        for (int i = 0; i < batch; ++i) {
+          sv.batch_iter = i;
+          sv.iteration();
+        }
+        sv.capturing = false;
+        sv.timers = nullptr;
+        g.timing = h->timing;
+        g.launches = sv.launches - before;
+        sv.launches = before;
+        cudaError_t e = cudaStreamEndCapture(h->s, &graph);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          g.exec = nullptr;
+          return cuda_fail(h, e, "cudaGraphInstantiate");
+        }
+        g.p = p;
+        g.method = (int)method;
+        g.batch = batch;
+        g.X = dX;
+        g.gen = h->gen;
+      }
+    }
+    int iter_before = 0;
+    for (int done_iters = 0;; done_iters += batch) {
+      const std::vector<Timer>* timers = nullptr;
+      if (use_graph) {
+        CK(h, cudaGraphLaunch(h->graph.exec, h->s));
+        sv.launches += h->graph.launches;
+        h->stat_replays++;
+        timers = &h->graph.timers;
+      } else {
+        direct_timers.clear();
+        if (h->timing) {
+          h->evnext = 0;
+          sv.timers = &direct_timers;
+        }
+        for (int i = 0; i < batch; ++i) {
+          sv.batch_iter = i;
+          sv.iteration();
+        }
+        sv.timers = nullptr;
+        CK(h, cudaGetLastError());
+        timers = &direct_timers;
+      }
+      CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+      CK(h, cudaStreamSynchronize(h->s));
+      if (h->timing && timers) {
+        // kernels of iterations past the end returned at once: not counted
+        const int ran = h->h_ctrl->iter - iter_before;
+        for (const Timer& t : *timers) {
+          if (t.iter >= ran) continue;
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+            h->kt_ms[t.kind] += ms;
+            h->kt_n[t.kind] += 1;
+          } else {
+            cudaGetLastError();   // timing is best effort; never fail the solve for it
+          }
+        }
+      }
+      iter_before = h->h_ctrl->iter;
+      if (h->h_ctrl->done) break;
+      if (done_iters > maxit + 2 * batch) {
+        h->err = "iteration control did not stop";
+        return BLCOC_ERR_CUDA;
+      }
+    }
+  }
+  // true residual of the returned iterate
+  sv.B = dB;
+  sv.X = dX;
+  sv.true_residual();
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+  CK(h, cudaStreamSynchronize(h->s));
+  const Ctrl c = *h->h_ctrl;
+  h->iters = zero_rhs ? 0 : c.iter;
+  const double nb = std::sqrt(c.sumsq_b);
+  h->trr = zero_rhs ? 0.0 : (nb > 0 ? c.trr / nb : NAN);
+  h->hist_h.assign(zero_rhs ? 1 : c.nhist, 0.0);
+  if (!zero_rhs && c.nhist > 0)
+    CK(h, cudaMemcpy(h->hist_h.data(), h->hist, (size_t)c.nhist * sizeof(double), cudaMemcpyDeviceToHost));
+  if (zero_rhs) h->relres = 0.0;
+  else if (c.done == 3) h->relres = c.nhist > 0 ? h->hist_h[c.nhist - 1] : h->trr;
+  else h->relres = c.relres;
+  h->xi_h.assign(2 * p * p, 0.0);
+  CK(h, cudaMemcpy(h->xi_h.data(), h->mats + M_XI * PMAX * PMAX, (size_t)p * p * sizeof(double2),
+                   cudaMemcpyDeviceToHost));
+  if (hostX) CK(h, cudaMemcpyAsync(X, h->Xst, bytes, cudaMemcpyDeviceToHost, h->s));
+  CK(h, cudaEventRecord(h->ev, h->s));
+  CK(h, cudaStreamWaitEvent(h->user_stream, h->ev, 0));
+  CK(h, cudaStreamSynchronize(h->s));
+  h->stat_launches = sv.launches;
+  if (zero_rhs) return BLCOC_OK;
+  switch (c.done) {
+    case 1: return BLCOC_OK;
+    case 2: return BLCOC_NOT_CONVERGED;
+    case 3: {
+      char buf[128];
+      snprintf(buf, sizeof buf, "breakdown at iteration %d (site %d)", c.iter, c.bd_code);
+      h->err = buf;
+      return BLCOC_BREAKDOWN;
+    }
+    default: h->err = "solve ended in an unknown state"; return BLCOC_ERR_CUDA;
+  }
+}
+
+blcoc_status blcoc_get_info(blcoc_handle h, int* iters, double* relres_recursive, double* relres_true, double* hist,
+                            int hist_len) {
+  if (!h) return invalid(h, "NULL handle");
+  if (iters) *iters = h->iters;
+  if (relres_recursive) *relres_recursive = h->relres;
+  if (relres_true) *relres_true = h->trr;
+  if (hist && hist_len > 0) {
+    const int k = (int)h->hist_h.size() < hist_len ? (int)h->hist_h.size() : hist_len;
+    for (int i = 0; i < k; ++i) hist[i] = h->hist_h[i];
+  }
+  return BLCOC_OK;
+}
+
+blcoc_status blcoc_get_xi(blcoc_handle h, double* xi_out) {
+  if (!h || !xi_out) return invalid(h, "NULL argument");
+  for (size_t i = 0; i < h->xi_h.size(); ++i) xi_out[i] = h->xi_h[i];
+  return BLCOC_OK;
+}
+
+}  // extern "C"

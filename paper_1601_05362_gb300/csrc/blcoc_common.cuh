@@ -1,0 +1,119 @@
+// Shared device-side definitions of libblcoc: control block, small-matrix slots,
+// complex FP64 arithmetic, and the launch-table type the host driver dispatches on.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace blcoc {
+
+constexpr int PMAX = 32;        // largest block width (right-hand sides)
+constexpr int CHUNK = 32;       // rows per warp chunk: lane i of a warp owns row i
+constexpr int NWARP = 4;        // warps per CTA in the row-pass kernels (one per SMSP)
+constexpr int RED_SPLIT = 16;   // first-stage slices of the cross-CTA Gram reduction
+constexpr int SMALL_THREADS = 256;
+
+// Device-resident control block of one solve.  Kernels of an iteration return at once
+// when `done` is non-zero, so a batch of queued iterations past convergence is a no-op.
+struct Ctrl {
+  int done;       // 0 running, 1 converged, 2 iteration limit, 3 breakdown
+  int iter;       // m: X holds X_m
+  int maxit;
+  int bd_code;    // breakdown site: 1 setup QR, 2 alpha solve, 3 QR, 4 beta solve, 5 non-finite xi
+  int nhist;      // entries of the residual history written so far
+  int pad_i;
+  double tol;
+  double nb;      // ||B||_F
+  double relres;  // ||xi_iter||_F / ||B||_F
+  double trr;     // ||B - A X||_F (after the final residual pass)
+  double sumsq_b; // sum |B_ij|^2 (setup)
+  double pad[2];
+};
+
+// p x p complex matrices live in one device array of slots, each PMAX*PMAX entries,
+// row-major with row stride p (dense p x p in the first p*p entries).
+enum MatSlot {
+  M_XI = 0,      // xi_m
+  M_TAU,         // tau_{m+1} (upper triangular, real positive diagonal)
+  M_TINV,        // T = tau^{-1} of the current W (Q = W T)
+  M_ALPHA,       // alpha'_m
+  M_ALPHAXI,     // alpha'_m xi_m
+  M_BETA,        // beta'_m
+  M_H,           // cocr: H_m = Q_m^T V_m;  cocg: G_QQ = Q_m^T Q_m
+  M_G1,          // cocr: U^T U;  cocg: S^T A S
+  M_NSLOTS
+};
+
+// Gram layouts in the partial buffers: "tri" = upper triangle a <= b, row-major
+// (p(p+1)/2 entries); "full" = p*p row-major.
+__host__ __device__ inline int tri_count(int p) { return p * (p + 1) / 2; }
+
+// ----------------------------------------------------------------------------- complex
+__device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
+
+// acc += a * b  (4 DFMA)
+__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+// acc -= a * b
+__device__ __forceinline__ void cmsub(double2& acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cmac_conj(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// ----------------------------------------------------------------------------- launch table
+struct CsrDev {
+  int64_t n;
+  int64_t nnz;
+  const int* rp;
+  const int* ci;
+  const double2* va;
+};
+
+struct PassArgs {
+  CsrDev A;
+  int p;
+  double2* W;
+  double2* S;
+  double2* U;
+  double2* V;         // cocr: V;  cocg: A S
+  double2* X;
+  const double2* B;
+  const double2* mats;
+  double2* partials;  // [grid][ne]
+  int ne;             // partial entries per CTA
+  Ctrl* ctrl;
+  int flag;           // kernel-specific switch (first pass / apply T / norm only / cocg grams)
+  int grid;
+};
+
+using LaunchFn = void (*)(const PassArgs&, cudaStream_t);
+
+// Row-pass kernels for one compile-time block width PP (p <= PP).
+struct KernelSet {
+  LaunchFn resid;        // R = B - A X; grams R^H R (+ R^T R if flag&2); norms; flag&1: norm only
+  LaunchFn spmm_gram;    // Y = A W; gram W^T Y; out = Y T (flag=1) or Y (flag=0)
+  LaunchFn spmm_plain;   // Y = A W (no gram), for blcoc_spmm
+  LaunchFn cocr_passA;   // W <- W T - U alpha'; gram W^H W
+  LaunchFn cocr_passC;   // Q = W T; X += S alpha'xi; S = Q + S beta'; U = V + U beta'; gram U^T U
+  LaunchFn cocg_pass1;   // Q = W T; W <- Q - (AS) alpha'; X += S alpha'xi; grams W^H W, W^T W
+  LaunchFn cocg_pass2;   // S <- W T + S beta'
+  int (*grid)(int64_t n, int kind, int num_sms);
+  void (*prepare)();     // set the dynamic shared-memory limits (once per device)
+};
+
+template <int PP> const KernelSet& kernel_set();
+
+}  // namespace blcoc

@@ -1,0 +1,608 @@
+// Row-pass kernels of bl_cocg_rq / bl_cocr_rq (Algorithms 2-3, Sec. 2.2), templated on
+// the block width PP (the solve's p satisfies p <= PP).
+//
+// Work decomposition.  On GB300 every FP64 operation of this path is issued by the FP64
+// pipe (about 2 DFMA per clock per SM), which binds long before HBM does; the design
+// therefore spends no FP64 operation it does not need:
+//   * a warp owns chunks of 32 consecutive rows; the chunk's n x p slices are staged in
+//     the warp's own shared-memory tiles, so warps never wait on each other;
+//   * p x p right-multiplications (Y <- Y M) run with lane = row: all lanes walk the same
+//     (k, j) sequence, so the upper-triangular tau^{-1} applies cost exactly p(p+1)/2
+//     complex MACs per row and the p x p factor is a shared-memory broadcast;
+//   * Gram products G = Y^T Z (or Y^H Z) over the chunk run with lane = Gram entry;
+//     symmetric / Hermitian Grams compute only the upper triangle;
+//   * per-CTA Gram partials are summed in a fixed order (first here, then by a
+//     deterministic two-stage reduction), so results are bitwise reproducible.
+// Tiles are [k][32 rows] with the row index XOR-swizzled by (k & 7): lane = row reads,
+// lane = entry reads and the coalesced global <-> shared transposes are all free of
+// shared-memory bank conflicts.
+#pragma once
+
+#include "blcoc_common.cuh"
+
+namespace blcoc {
+
+template <int PP>
+struct Geo {
+  static constexpr int TILE = PP * CHUNK;                      // double2 per staged block
+  static constexpr int NFULL = (PP * PP + 31) / 32;            // gram slots per lane, full
+  static constexpr int NTRI = (PP * (PP + 1) / 2 + 31) / 32;   // gram slots per lane, triangle
+  static constexpr int JB = PP >= 8 ? 8 : PP;                  // output columns per apply sweep
+  static constexpr bool MATS_SMEM = PP <= 16;                  // p x p factors staged in smem
+  static constexpr int LPR = PP < 32 ? PP : 32;                // lanes per row in the CSR gather
+  static constexpr int RPI = 32 / LPR;                         // rows per gather instruction
+};
+
+__device__ __forceinline__ int tix(int k, int r) { return k * CHUNK + (r ^ (k & 7)); }
+
+// ---------------------------------------------------------------------------------- tiles
+// Coalesced load of rows [r0, r0+32) (clipped to n) of a row-major n x p block into a
+// swizzled tile; rows past n are zero.
+template <int PP>
+__device__ __forceinline__ void load_tile(double2* t, const double2* __restrict__ g, int64_t r0, int64_t n, int p,
+                                          int lane) {
+  const int rows = (int)min((int64_t)CHUNK, n - r0);
+  const int total = CHUNK * p;
+  const int valid = rows * p;
+  const double2* src = g + r0 * p;
+  for (int e = lane; e < total; e += 32) {
+    const int r = e / p, k = e - r * p;
+    t[tix(k, r)] = (e < valid) ? src[e] : cz();
+  }
+}
+
+template <int PP>
+__device__ __forceinline__ void store_tile(double2* __restrict__ g, const double2* t, int64_t r0, int64_t n, int p,
+                                           int lane) {
+  const int rows = (int)min((int64_t)CHUNK, n - r0);
+  const int valid = rows * p;
+  double2* dst = g + r0 * p;
+  for (int e = lane; e < valid; e += 32) {
+    const int r = e / p, k = e - r * p;
+    dst[e] = t[tix(k, r)];
+  }
+}
+
+// Stage a p x p factor (row stride p in global) as PP x PP, zero padded.
+template <int PP>
+__device__ __forceinline__ void load_mat(double2* s, const double2* __restrict__ g, int p) {
+  for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
+    const int k = e / PP, j = e - k * PP;
+    s[e] = (k < p && j < p) ? g[k * p + j] : cz();
+  }
+}
+
+// Factor access: shared memory (stride PP) or global memory through the read-only path.
+template <int PP>
+struct Fac {
+  const double2* m;
+  int ld;
+  __device__ __forceinline__ double2 operator()(int k, int j) const {
+    if constexpr (Geo<PP>::MATS_SMEM) return m[k * PP + j];
+    else return __ldg(m + k * ld + j);
+  }
+};
+
+// ---------------------------------------------------------------------------------- applies
+// t <- t * T with T upper triangular (lane = row).  Columns are produced from the last
+// block to the first, so a column slot is overwritten only after every later column
+// that needs it has been formed.  Cost: exactly sum_j (j+1) complex MACs per row.
+template <int PP>
+__device__ __forceinline__ void tri_apply_inplace(double2* t, const Fac<PP>& T, int p, int lane) {
+  constexpr int JB = Geo<PP>::JB;
+  for (int j0 = ((p - 1) / JB) * JB; j0 >= 0; j0 -= JB) {
+    double2 acc[JB];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) acc[jj] = cz();
+    for (int k = 0; k < j0; ++k) {
+      const double2 y = t[tix(k, lane)];
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) cmac(acc[jj], y, T(k, j0 + jj));
+    }
+#pragma unroll
+    for (int kk = 0; kk < JB; ++kk) {
+      if (j0 + kk < p) {
+        const double2 y = t[tix(j0 + kk, lane)];
+#pragma unroll
+        for (int jj = kk; jj < JB; ++jj) cmac(acc[jj], y, T(j0 + kk, j0 + jj));
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj)
+      if (j0 + jj < p) t[tix(j0 + jj, lane)] = acc[jj];
+  }
+}
+
+// out <- base + in * M  (SUB: base - in * M), lane = row.  `out` may be `base`
+// (each column of base is read only for the same column of out) but not `in`.
+template <int PP, bool SUB>
+__device__ __forceinline__ void apply_full(double2* out, const double2* base, const double2* in, const Fac<PP>& M,
+                                           int p, int lane) {
+  constexpr int JB = Geo<PP>::JB;
+  for (int j0 = 0; j0 < p; j0 += JB) {
+    double2 acc[JB];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) acc[jj] = (j0 + jj < p) ? base[tix(j0 + jj, lane)] : cz();
+    for (int k = 0; k < p; ++k) {
+      const double2 y = in[tix(k, lane)];
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) {
+        if constexpr (SUB) cmsub(acc[jj], y, M(k, j0 + jj));
+        else cmac(acc[jj], y, M(k, j0 + jj));
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj)
+      if (j0 + jj < p) out[tix(j0 + jj, lane)] = acc[jj];
+  }
+}
+
+// ---------------------------------------------------------------------------------- grams
+enum GramKind { G_FULL = 0, G_SYM = 1, G_HERM = 2 };
+
+template <int NS>
+struct GramAcc {
+  double2 acc[NS];
+  short a[NS], b[NS];
+  int E;
+  __device__ __forceinline__ void init(int kind, int p, int lane) {
+    E = (kind == G_FULL) ? p * p : tri_count(p);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      acc[i] = cz();
+      const int e = lane + 32 * i;
+      int aa = 0, bb = 0;
+      if (e < E) {
+        if (kind == G_FULL) {
+          aa = e / p;
+          bb = e - aa * p;
+        } else {
+          int rem = e;
+          while (rem >= p - aa) { rem -= p - aa; ++aa; }
+          bb = aa + rem;
+        }
+      }
+      a[i] = (short)aa;
+      b[i] = (short)bb;
+    }
+  }
+  // acc[e] += sum_r op(Y[r][a_e]) Z[r][b_e] over the 32 rows of a chunk
+  template <bool CONJ>
+  __device__ __forceinline__ void add(const double2* Y, const double2* Z, int lane) {
+#pragma unroll 2
+    for (int r = 0; r < CHUNK; ++r) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        if (lane + 32 * i < E) {
+          const double2 y = Y[tix(a[i], r)];
+          const double2 z = Z[tix(b[i], r)];
+          if constexpr (CONJ) cmac_conj(acc[i], y, z);
+          else cmac(acc[i], y, z);
+        }
+      }
+    }
+  }
+};
+
+// Sum the warps' accumulators of one Gram in a fixed order and write the CTA partial.
+// `red` is shared scratch of at least NWARP*E double2; caller syncs before reuse.
+template <int NS>
+__device__ __forceinline__ void cta_write_gram(const GramAcc<NS>& g, double2* red, double2* __restrict__ out,
+                                               int warp, int lane) {
+#pragma unroll
+  for (int i = 0; i < NS; ++i) {
+    const int e = lane + 32 * i;
+    if (e < g.E) red[warp * g.E + e] = g.acc[i];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < g.E; e += blockDim.x) {
+    double2 s = red[e];
+    for (int w = 1; w < NWARP; ++w) {
+      s.x += red[w * g.E + e].x;
+      s.y += red[w * g.E + e].y;
+    }
+    out[e] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------- gather
+// Y[r][k] = sum_j a_{row,j} X[j][k] (lanes = columns, PP/32 rows per instruction), written
+// to a swizzled tile.  RESID: Y = B - A X, also accumulating |B|^2 and |Y|^2 per lane.
+template <int PP, bool RESID>
+__device__ __forceinline__ void gather_rows(double2* Yt, const CsrDev& A, const double2* __restrict__ Xg,
+                                            const double2* __restrict__ Bg, int64_t r0, int p, int lane,
+                                            double& sb, double& sr) {
+  constexpr int LPR = Geo<PP>::LPR, RPI = Geo<PP>::RPI;
+  const int sub = lane / LPR, k = lane - sub * LPR;
+  for (int rr = 0; rr < CHUNK; rr += RPI) {
+    const int r = rr + sub;
+    const int64_t row = r0 + r;
+    double2 acc = cz();
+    if (row < A.n && k < p) {
+      if constexpr (RESID) {
+        acc = Bg[row * p + k];
+        sb = fma(acc.x, acc.x, sb);
+        sb = fma(acc.y, acc.y, sb);
+      }
+      const int beg = A.rp[row], end = A.rp[row + 1];
+      for (int j = beg; j < end; ++j) {
+        const int c = __ldg(A.ci + j);
+        const double2 a = __ldg(A.va + j);
+        const double2 x = Xg[(int64_t)c * p + k];
+        if constexpr (RESID) cmsub(acc, a, x);
+        else cmac(acc, a, x);
+      }
+      if constexpr (RESID) {
+        sr = fma(acc.x, acc.x, sr);
+        sr = fma(acc.y, acc.y, sr);
+      }
+    }
+    Yt[tix(k, r)] = acc;
+  }
+}
+
+__device__ __forceinline__ double warp_sum_fixed(double v) {
+  // fixed butterfly order: deterministic
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------- kernels
+// PassArgs::flag bits
+constexpr int F_FIRST = 1;      // setup variant of a pass / norm-only residual / apply T
+constexpr int F_SYM2 = 2;       // residual pass: also R^T R
+constexpr int F_FORCE = 16;     // run even when the control block says the solve is done
+#define BLCOC_PROLOGUE                                  \
+  if (!(a.flag & F_FORCE) && a.ctrl->done) return;      \
+  extern __shared__ __align__(16) double2 smem[];       \
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31; \
+  const int64_t n = a.A.n;                              \
+  const int p = a.p;                                    \
+  const int64_t nchunks = (n + CHUNK - 1) / CHUNK;      \
+  const int64_t cstride = (int64_t)gridDim.x * NWARP;
+
+// R = B - A X (Sec. 3 residual, setup line 1 of Algorithms 2-3).
+// flag&1: norms only; flag&2: also R^T R (cocg).  Partials: [R^H R tri][R^T R tri][sum|B|^2, sum|R|^2]
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  const bool norm_only = a.flag & 1, sym2 = a.flag & 2;
+  double2* tR = smem + warp * G::TILE;
+  double2* red = smem;
+  GramAcc<G::NTRI> gh, gs;
+  gh.init(G_HERM, p, lane);
+  gs.init(G_SYM, p, lane);
+  double sb = 0.0, sr = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    gather_rows<PP, true>(tR, a.A, a.X, a.B, r0, p, lane, sb, sr);
+    if (!norm_only) {
+      __syncwarp();
+      gh.template add<true>(tR, tR, lane);
+      if (sym2) gs.template add<false>(tR, tR, lane);
+      store_tile<PP>(a.W, tR, r0, n, p, lane);
+    }
+    __syncwarp();
+  }
+  sb = warp_sum_fixed(sb);
+  sr = warp_sum_fixed(sr);
+  __syncthreads();
+  double2* out = a.partials + (int64_t)blockIdx.x * a.ne;
+  const int E = tri_count(p);
+  if (!norm_only) {
+    cta_write_gram(gh, red, out, warp, lane);
+    if (sym2) cta_write_gram(gs, red, out + E, warp, lane);
+  }
+  if (lane == 0) red[warp] = make_double2(sb, sr);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 s = red[0];
+    for (int w = 1; w < NWARP; ++w) { s.x += red[w].x; s.y += red[w].y; }
+    out[2 * E] = s;
+  }
+}
+
+// Y = A W over the chunk, W = the block in a.W; gram W^T Y (symmetric since A = A^T);
+// out = Y T (flag=1, cocr: V = A Q = (A W) tau^{-1}) or out = Y (flag=0, cocg: a.W = S,
+// out = A S).  Partials: [W^T Y tri].
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  double2* T_s = smem;
+  double2* tiles = smem + (G::MATS_SMEM ? PP * PP : 0);
+  double2* tY = tiles + warp * 2 * G::TILE;
+  double2* tW = tY + G::TILE;
+  const bool applyT = a.flag & 1;
+  if constexpr (G::MATS_SMEM) {
+    load_mat<PP>(T_s, a.mats + M_TINV * PMAX * PMAX, p);
+    __syncthreads();
+  }
+  Fac<PP> T{G::MATS_SMEM ? T_s : a.mats + M_TINV * PMAX * PMAX, p};
+  GramAcc<G::NTRI> g;
+  g.init(G_SYM, p, lane);
+  double dummy0 = 0.0, dummy1 = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    gather_rows<PP, false>(tY, a.A, a.W, nullptr, r0, p, lane, dummy0, dummy1);
+    load_tile<PP>(tW, a.W, r0, n, p, lane);
+    __syncwarp();
+    g.template add<false>(tW, tY, lane);
+    if (applyT) {
+      tri_apply_inplace<PP>(tY, T, p, lane);
+      __syncwarp();
+    }
+    store_tile<PP>(a.V, tY, r0, n, p, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+}
+
+// Y = A W, nothing else (blcoc_spmm).
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  double2* tY = smem + warp * G::TILE;
+  double d0 = 0.0, d1 = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    gather_rows<PP, false>(tY, a.A, a.W, nullptr, r0, p, lane, d0, d1);
+    __syncwarp();
+    store_tile<PP>(a.V, tY, r0, n, p, lane);
+    __syncwarp();
+  }
+}
+
+// bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): with Q_m = W_m T_m,
+// W_{m+1} = Q_m - U_m alpha'_m, in place; gram W^H W for the Cholesky QR.
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  double2* mT = smem;
+  double2* mA = smem + PP * PP;
+  double2* tiles = smem + (G::MATS_SMEM ? 2 * PP * PP : 0);
+  double2* tW = tiles + warp * 2 * G::TILE;
+  double2* tU = tW + G::TILE;
+  if constexpr (G::MATS_SMEM) {
+    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
+    load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
+    __syncthreads();
+  }
+  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
+  Fac<PP> AL{G::MATS_SMEM ? mA : a.mats + M_ALPHA * PMAX * PMAX, p};
+  GramAcc<G::NTRI> g;
+  g.init(G_HERM, p, lane);
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(tW, a.W, r0, n, p, lane);
+    load_tile<PP>(tU, a.U, r0, n, p, lane);
+    __syncwarp();
+    tri_apply_inplace<PP>(tW, T, p, lane);            // Q_m
+    apply_full<PP, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
+    __syncwarp();
+    g.template add<true>(tW, tW, lane);
+    store_tile<PP>(a.W, tW, r0, n, p, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+}
+
+// bl_cocr_rq pass C (Algorithm 3, lines 5, 9, 10) with Q_{m+1} = W_{m+1} T_{m+1}:
+//   X_{m+1} = X_m + S_m (alpha'_m xi_m);  S_{m+1} = Q_{m+1} + S_m beta'_m;
+//   U_{m+1} = V_{m+1} + U_m beta'_m;  gram U^T U (next alpha').
+// flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  const bool first = a.flag & 1;
+  double2* mT = smem;
+  double2* mAX = smem + PP * PP;
+  double2* mB = smem + 2 * PP * PP;
+  double2* tiles = smem + (G::MATS_SMEM ? 3 * PP * PP : 0);
+  double2* b0 = tiles + warp * 3 * G::TILE;
+  double2* b1 = b0 + G::TILE;
+  double2* b2 = b1 + G::TILE;
+  if constexpr (G::MATS_SMEM) {
+    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
+    load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
+    load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
+    __syncthreads();
+  }
+  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
+  Fac<PP> AX{G::MATS_SMEM ? mAX : a.mats + M_ALPHAXI * PMAX * PMAX, p};
+  Fac<PP> BE{G::MATS_SMEM ? mB : a.mats + M_BETA * PMAX * PMAX, p};
+  GramAcc<G::NTRI> g;
+  g.init(G_SYM, p, lane);
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(b0, a.W, r0, n, p, lane);
+    if (!first) {
+      load_tile<PP>(b1, a.S, r0, n, p, lane);
+      load_tile<PP>(b2, a.X, r0, n, p, lane);
+    }
+    __syncwarp();
+    tri_apply_inplace<PP>(b0, T, p, lane);             // Q_{m+1}
+    if (!first) {
+      apply_full<PP, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
+      __syncwarp();
+      store_tile<PP>(a.X, b2, r0, n, p, lane);
+      __syncwarp();
+      apply_full<PP, false>(b2, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
+      __syncwarp();
+      store_tile<PP>(a.S, b2, r0, n, p, lane);
+    } else {
+      __syncwarp();
+      store_tile<PP>(a.S, b0, r0, n, p, lane);
+    }
+    __syncwarp();
+    load_tile<PP>(b1, a.V, r0, n, p, lane);
+    if (!first) load_tile<PP>(b2, a.U, r0, n, p, lane);
+    __syncwarp();
+    if (!first) {
+      apply_full<PP, false>(b1, b1, b2, BE, p, lane);  // U_{m+1} = V + U beta'
+      __syncwarp();
+    }
+    g.template add<false>(b1, b1, lane);
+    store_tile<PP>(a.U, b1, r0, n, p, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+}
+
+// bl_cocg_rq pass 1 (Algorithm 2, lines 5-6): with Q_m = W_m T_m,
+//   W_{m+1} = Q_m - (A S_m) alpha'_m (in place);  X_{m+1} = X_m + S_m (alpha'_m xi_m);
+//   grams W^H W (QR) and W^T W (Q^T Q of line 7).  Partials: [W^H W tri][W^T W tri].
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  double2* mT = smem;
+  double2* mAX = smem + PP * PP;
+  double2* mA = smem + 2 * PP * PP;
+  double2* tiles = smem + (G::MATS_SMEM ? 3 * PP * PP : 0);
+  double2* b0 = tiles + warp * 3 * G::TILE;
+  double2* b1 = b0 + G::TILE;
+  double2* b2 = b1 + G::TILE;
+  if constexpr (G::MATS_SMEM) {
+    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
+    load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
+    load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
+    __syncthreads();
+  }
+  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
+  Fac<PP> AX{G::MATS_SMEM ? mAX : a.mats + M_ALPHAXI * PMAX * PMAX, p};
+  Fac<PP> AL{G::MATS_SMEM ? mA : a.mats + M_ALPHA * PMAX * PMAX, p};
+  GramAcc<G::NTRI> gh, gs;
+  gh.init(G_HERM, p, lane);
+  gs.init(G_SYM, p, lane);
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(b0, a.W, r0, n, p, lane);
+    load_tile<PP>(b1, a.V, r0, n, p, lane);
+    __syncwarp();
+    tri_apply_inplace<PP>(b0, T, p, lane);             // Q_m
+    apply_full<PP, true>(b0, b0, b1, AL, p, lane);     // W_{m+1} = Q_m - A S_m alpha'
+    __syncwarp();
+    load_tile<PP>(b1, a.S, r0, n, p, lane);
+    load_tile<PP>(b2, a.X, r0, n, p, lane);
+    __syncwarp();
+    apply_full<PP, false>(b2, b2, b1, AX, p, lane);    // X_{m+1}
+    gh.template add<true>(b0, b0, lane);
+    gs.template add<false>(b0, b0, lane);
+    __syncwarp();
+    store_tile<PP>(a.X, b2, r0, n, p, lane);
+    store_tile<PP>(a.W, b0, r0, n, p, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  double2* out = a.partials + (int64_t)blockIdx.x * a.ne;
+  cta_write_gram(gh, tiles, out, warp, lane);
+  cta_write_gram(gs, tiles, out + tri_count(p), warp, lane);
+}
+
+// bl_cocg_rq pass 2 (Algorithm 2, line 8): S_{m+1} = W_{m+1} T_{m+1} + S_m beta'_m.
+// flag=1 (setup, line 2): S_0 = Q_0 = W_0 T_0.
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
+  BLCOC_PROLOGUE
+  using G = Geo<PP>;
+  const bool first = a.flag & 1;
+  double2* mT = smem;
+  double2* mB = smem + PP * PP;
+  double2* tiles = smem + (G::MATS_SMEM ? 2 * PP * PP : 0);
+  double2* b0 = tiles + warp * 2 * G::TILE;
+  double2* b1 = b0 + G::TILE;
+  if constexpr (G::MATS_SMEM) {
+    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
+    load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
+    __syncthreads();
+  }
+  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
+  Fac<PP> BE{G::MATS_SMEM ? mB : a.mats + M_BETA * PMAX * PMAX, p};
+  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(b0, a.W, r0, n, p, lane);
+    if (!first) load_tile<PP>(b1, a.S, r0, n, p, lane);
+    __syncwarp();
+    tri_apply_inplace<PP>(b0, T, p, lane);            // Q_{m+1}
+    if (!first) apply_full<PP, false>(b0, b0, b1, BE, p, lane);
+    __syncwarp();
+    store_tile<PP>(a.S, b0, r0, n, p, lane);
+    __syncwarp();
+  }
+}
+
+#undef BLCOC_PROLOGUE
+
+// ---------------------------------------------------------------------------------- launch
+enum PassKind { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_NKIND };
+
+template <int PP>
+constexpr size_t pass_smem(int kind) {
+  using G = Geo<PP>;
+  const size_t mat = (size_t)PP * PP * sizeof(double2);
+  const size_t tile = (size_t)G::TILE * sizeof(double2);
+  const int nmats[K_NKIND] = {0, 1, 0, 2, 3, 3, 2};
+  const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2};
+  return (G::MATS_SMEM ? nmats[kind] * mat : 0) + (size_t)NWARP * ntiles[kind] * tile;
+}
+
+template <int PP>
+int pass_grid(int64_t n, int kind, int num_sms) {
+  const size_t smem = pass_smem<PP>(kind);
+  int per_sm = (int)((227u * 1024u) / (smem + 1024u));
+  per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+  const int64_t nchunks = (n + CHUNK - 1) / CHUNK;
+  int64_t want = (nchunks + NWARP - 1) / NWARP;
+  int64_t g = (int64_t)num_sms * per_sm;
+  if (want < g) g = want;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int PP, int KIND, void (*K)(const PassArgs)>
+void launch_pass(const PassArgs& a, cudaStream_t s) {
+  K<<<a.grid, NWARP * 32, pass_smem<PP>(KIND), s>>>(a);
+}
+
+template <int PP>
+void prepare_pass_kernels() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_resid<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_RESID));
+  cudaFuncSetAttribute(k_spmm_gram<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_SPMM_GRAM));
+  cudaFuncSetAttribute(k_spmm_plain<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP>(K_SPMM_PLAIN));
+  cudaFuncSetAttribute(k_cocr_passA<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCR_A));
+  cudaFuncSetAttribute(k_cocr_passC<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCR_C));
+  cudaFuncSetAttribute(k_cocg_pass1<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCG_1));
+  cudaFuncSetAttribute(k_cocg_pass2<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCG_2));
+  done[dev] = true;
+}
+
+template <int PP>
+const KernelSet& kernel_set() {
+  static const KernelSet ks = {
+      &launch_pass<PP, K_RESID, k_resid<PP>>,
+      &launch_pass<PP, K_SPMM_GRAM, k_spmm_gram<PP>>,
+      &launch_pass<PP, K_SPMM_PLAIN, k_spmm_plain<PP>>,
+      &launch_pass<PP, K_COCR_A, k_cocr_passA<PP>>,
+      &launch_pass<PP, K_COCR_C, k_cocr_passC<PP>>,
+      &launch_pass<PP, K_COCG_1, k_cocg_pass1<PP>>,
+      &launch_pass<PP, K_COCG_2, k_cocg_pass2<PP>>,
+      &pass_grid<PP>,
+      &prepare_pass_kernels<PP>,
+  };
+  return ks;
+}
+
+}  // namespace blcoc

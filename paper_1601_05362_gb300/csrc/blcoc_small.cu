@@ -1,0 +1,512 @@
+// p x p stages of bl_cocg_rq / bl_cocr_rq (Algorithms 2-3, Sec. 2.2), one CTA each,
+// plus the deterministic cross-CTA Gram reduction and the CSR checks of blcoc_create.
+//
+// The p x p systems are complex symmetric, not Hermitian (their matrices are bilinear
+// Grams Y^T Z), so they are solved by LU with partial pivoting (pivot = largest
+// |re| + |im| in the column, ties to the lowest row).  The thin QR of the residual
+// block is a Cholesky QR: tau^H tau = W^H W with tau upper triangular and a real
+// positive diagonal, T = tau^{-1}.
+#include "blcoc_common.cuh"
+#include "blcoc_small.h"
+
+namespace blcoc {
+
+constexpr int LD = PMAX;   // leading dimension of p x p matrices in shared memory
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 crecip(double2 z) {
+  const double d = z.x * z.x + z.y * z.y;
+  return make_double2(z.x / d, -z.y / d);
+}
+__device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
+__device__ __forceinline__ bool cfinite(double2 z) { return isfinite(z.x) && isfinite(z.y); }
+
+// ------------------------------------------------------------------------ cross-CTA reduce
+// stage1[s][c] = sum of partials[q][c] over q in slice s (fixed order).
+__global__ void k_reduce_stage1(const double* __restrict__ partials, int nparts, int ncomp,
+                                double* __restrict__ stage1, const Ctrl* ctrl) {
+  if (ctrl != nullptr && ctrl->done) return;
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  if (c >= ncomp) return;
+  const int s = blockIdx.y;
+  const int q0 = (int)((int64_t)s * nparts / RED_SPLIT), q1 = (int)((int64_t)(s + 1) * nparts / RED_SPLIT);
+  double acc = 0.0;
+  for (int q = q0; q < q1; ++q) acc += partials[(int64_t)q * ncomp + c];
+  stage1[(int64_t)s * ncomp + c] = acc;
+}
+
+// Second stage, inside the small kernels: gs[c] = sum_s stage1[s][c].
+__device__ void sum_stage1(const double* __restrict__ stage1, int ncomp, double* gs) {
+  for (int c = threadIdx.x; c < ncomp; c += blockDim.x) {
+    double acc = 0.0;
+    for (int s = 0; s < RED_SPLIT; ++s) acc += stage1[(int64_t)s * ncomp + c];
+    gs[c] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void tri_decode(int e, int p, int& a, int& b) {
+  int aa = 0, rem = e;
+  while (rem >= p - aa) { rem -= p - aa; ++aa; }
+  a = aa;
+  b = aa + rem;
+}
+
+// Triangle (upper, row-major) -> full p x p; herm: M[b][a] = conj(M[a][b]).
+__device__ void expand_tri(const double* gs, double2* M, int p, bool herm) {
+  const int E = tri_count(p);
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    int a, b;
+    tri_decode(e, p, a, b);
+    const double2 v = make_double2(gs[2 * e], gs[2 * e + 1]);
+    M[a * LD + b] = v;
+    if (a != b) M[b * LD + a] = herm ? make_double2(v.x, -v.y) : v;
+  }
+  __syncthreads();
+}
+
+__device__ void gload(double2* s, const double2* __restrict__ g, int p) {
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) s[(e / p) * LD + e % p] = g[e];
+  __syncthreads();
+}
+__device__ void gstore(double2* __restrict__ g, const double2* s, int p) {
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) g[e] = s[(e / p) * LD + e % p];
+  __syncthreads();
+}
+
+// C = op(A) op(B), op = transpose (no conjugation) when the flag is set; C must not alias.
+__device__ void matmul(double2* C, const double2* A, bool tA, const double2* B, bool tB, int p) {
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e % p;
+    double2 acc = cz();
+    for (int k = 0; k < p; ++k) {
+      const double2 a = tA ? A[k * LD + i] : A[i * LD + k];
+      const double2 b = tB ? B[j * LD + k] : B[k * LD + j];
+      cmac(acc, a, b);
+    }
+    C[i * LD + j] = acc;
+  }
+  __syncthreads();
+}
+
+__device__ double fro_norm(const double2* M, int p, double* red) {
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const double2 v = M[(e / p) * LD + e % p];
+    acc += v.x * v.x + v.y * v.y;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) s += red[t];
+    red[0] = sqrt(s);
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Right-looking Cholesky of a Hermitian G (upper triangle used, destroyed): tau^H tau = G.
+__device__ bool chol_upper(double2* G, double2* tau, int p, double* sh) {
+  for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) tau[e] = cz();
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = G[j * LD + j].x;
+      if (!(d > 0.0) || !isfinite(d)) {
+        sh[0] = 0.0;
+      } else {
+        const double r = sqrt(d);
+        tau[j * LD + j] = make_double2(r, 0.0);
+        sh[0] = 1.0 / r;
+      }
+    }
+    __syncthreads();
+    const double inv = sh[0];
+    if (inv == 0.0) return false;
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) {
+      const double2 g = G[j * LD + i];
+      tau[j * LD + i] = make_double2(g.x * inv, g.y * inv);
+    }
+    __syncthreads();
+    const int m = p - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, l = j + 1 + e % m;
+      if (l >= i) {
+        const double2 ti = tau[j * LD + i], tl = tau[j * LD + l];
+        double2 g = G[i * LD + l];
+        // g -= conj(ti) * tl
+        g.x -= ti.x * tl.x + ti.y * tl.y;
+        g.y -= ti.x * tl.y - ti.y * tl.x;
+        G[i * LD + l] = g;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
+}
+
+// T = tau^{-1} for upper-triangular tau with real positive diagonal.
+__device__ void tri_inv_upper(const double2* tau, double2* T, int p) {
+  for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) T[e] = cz();
+  __syncthreads();
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    T[j * LD + j] = make_double2(1.0 / tau[j * LD + j].x, 0.0);
+    for (int i = j - 1; i >= 0; --i) {
+      double2 s = cz();
+      for (int k = i + 1; k <= j; ++k) cmac(s, tau[i * LD + k], T[k * LD + j]);
+      const double d = -1.0 / tau[i * LD + i].x;
+      T[i * LD + j] = make_double2(s.x * d, s.y * d);
+    }
+  }
+  __syncthreads();
+}
+
+// Solve M Z = R in place (R <- Z), LU with partial pivoting; M is destroyed.
+__device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, int* ish) {
+  for (int k = 0; k < p; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = p;
+      for (int i = k + threadIdx.x; i < p; i += 32) {
+        const double v = cabs1(M[i * LD + k]);
+        if (v > best || (v == best && i < bi) || v != v) {
+          best = (v != v) ? INFINITY : v;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        ish[0] = bi;
+        ish[1] = (best > 0.0 && isfinite(best)) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    if (!ish[1]) return false;
+    const int piv = ish[0];
+    if (piv != k) {
+      for (int c = threadIdx.x; c < p + nrhs; c += blockDim.x) {
+        if (c < p) {
+          const double2 t = M[k * LD + c];
+          M[k * LD + c] = M[piv * LD + c];
+          M[piv * LD + c] = t;
+        } else {
+          const int cc = c - p;
+          const double2 t = R[k * LD + cc];
+          R[k * LD + cc] = R[piv * LD + cc];
+          R[piv * LD + cc] = t;
+        }
+      }
+      __syncthreads();
+    }
+    const double2 pinv = crecip(M[k * LD + k]);
+    for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) M[i * LD + k] = cmul(M[i * LD + k], pinv);
+    __syncthreads();
+    const int m = p - k - 1, w = m + nrhs;
+    for (int e = threadIdx.x; e < m * w; e += blockDim.x) {
+      const int i = k + 1 + e / w, c = e % w;
+      const double2 l = M[i * LD + k];
+      if (c < m) cmsub(M[i * LD + k + 1 + c], l, M[k * LD + k + 1 + c]);
+      else cmsub(R[i * LD + (c - m)], l, R[k * LD + (c - m)]);
+    }
+    __syncthreads();
+  }
+  for (int k = p - 1; k >= 0; --k) {
+    const double2 dinv = crecip(M[k * LD + k]);
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) R[k * LD + c] = cmul(R[k * LD + c], dinv);
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
+      const int i = e / nrhs, c = e % nrhs;
+      cmsub(R[i * LD + c], M[i * LD + k], R[k * LD + c]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < p * nrhs; e += blockDim.x)
+    if (!cfinite(R[(e / nrhs) * LD + e % nrhs])) ish[1] = 0;
+  __syncthreads();
+  return ish[1] != 0;
+}
+
+// ------------------------------------------------------------------------ shared layout
+struct SmallShared {
+  double gs[2 * (2 * PMAX * (PMAX + 1) / 2 + 2)];
+  double red[SMALL_THREADS];
+  int ish[4];
+  double2 m[6][LD * LD];
+};
+
+#define SMALL_PROLOGUE                                                  \
+  extern __shared__ __align__(16) unsigned char small_raw[];            \
+  SmallShared& S = *reinterpret_cast<SmallShared*>(small_raw);
+
+__device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s * PMAX * PMAX; }
+
+// Setup after the residual pass: ||B||_F, Q_0 xi_0 = R_0 (Cholesky QR), T_0 = xi_0^{-1};
+// cocg: G_QQ = Q_0^T Q_0 = T^T (R^T R) T.
+__global__ void k_small_setup(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+  SMALL_PROLOGUE
+  if (ctrl->done) return;
+  sum_stage1(stage1, ncomp, S.gs);
+  const int E = tri_count(p);
+  const double sb = S.gs[2 * (2 * E)];
+  if (threadIdx.x == 0) {
+    ctrl->sumsq_b = sb;
+    ctrl->nb = sqrt(sb);
+  }
+  if (!(sb > 0.0) || !isfinite(sb)) {
+    if (threadIdx.x == 0) {
+      ctrl->done = (sb == 0.0) ? 1 : 3;
+      ctrl->bd_code = (sb == 0.0) ? 0 : 5;
+    }
+    return;
+  }
+  expand_tri(S.gs, S.m[0], p, true);
+  if (!chol_upper(S.m[0], S.m[1], p, S.red)) {
+    if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 1; }
+    return;
+  }
+  tri_inv_upper(S.m[1], S.m[2], p);
+  gstore(slot(mats, M_XI), S.m[1], p);
+  gstore(slot(mats, M_TINV), S.m[2], p);
+  if (method == 0) {
+    expand_tri(S.gs + 2 * E, S.m[3], p, false);
+    matmul(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
+    matmul(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
+    gstore(slot(mats, M_H), S.m[5], p);
+  }
+}
+
+// cocr setup after A Q_0: H_0 = Q_0^T V_0 = T^T (W^T A W) T.
+__global__ void k_small_cocr_H0(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+  SMALL_PROLOGUE
+  if (ctrl->done) return;
+  sum_stage1(stage1, ncomp, S.gs);
+  expand_tri(S.gs, S.m[0], p, false);
+  gload(S.m[1], slot(mats, M_TINV), p);
+  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
+  matmul(S.m[3], S.m[2], false, S.m[1], false, p);
+  gstore(slot(mats, M_H), S.m[3], p);
+}
+
+// Top of iteration m (Algorithms 2-3, lines 3-4): record ||xi_m||_F/||B||_F, stop if
+// <= tol or m = maxit; else alpha'_m = G1^{-1} RHS with G1 = U^T U (cocr) or S^T A S
+// (cocg) and RHS = Q^T V (cocr) or Q^T Q (cocg); also alpha'_m xi_m.
+__global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, double* hist) {
+  SMALL_PROLOGUE
+  if (ctrl->done) return;
+  const int m = ctrl->iter;
+  gload(S.m[0], slot(mats, M_XI), p);
+  const double rel = fro_norm(S.m[0], p, S.red) / ctrl->nb;
+  if (threadIdx.x == 0) {
+    hist[m] = rel;
+    ctrl->relres = rel;
+    ctrl->nhist = m + 1;
+  }
+  if (!isfinite(rel)) {
+    if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 5; }
+    return;
+  }
+  if (rel <= ctrl->tol) {
+    if (threadIdx.x == 0) ctrl->done = 1;
+    return;
+  }
+  if (m >= ctrl->maxit) {
+    if (threadIdx.x == 0) ctrl->done = 2;
+    return;
+  }
+  sum_stage1(stage1, ncomp, S.gs);
+  expand_tri(S.gs, S.m[1], p, false);     // G1 (symmetric)
+  gload(S.m[2], slot(mats, M_H), p);      // RHS
+  if (!lu_solve(S.m[1], S.m[2], p, p, S.red, S.ish)) {
+    if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 2; }
+    return;
+  }
+  gstore(slot(mats, M_ALPHA), S.m[2], p);
+  matmul(S.m[3], S.m[2], false, S.m[0], false, p);
+  gstore(slot(mats, M_ALPHAXI), S.m[3], p);
+  if (threadIdx.x == 0) ctrl->iter = m + 1;
+}
+
+// After W_{m+1} (Algorithms 2-3, line 6): Cholesky QR tau, T = tau^{-1},
+// xi_{m+1} = tau xi_m.  cocg also does line 7: G_QQ+ = T^T (W^T W) T and
+// beta' = G_QQ^{-1} tau^T G_QQ+.
+__global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+  SMALL_PROLOGUE
+  if (ctrl->done) return;
+  sum_stage1(stage1, ncomp, S.gs);
+  expand_tri(S.gs, S.m[0], p, true);
+  if (!chol_upper(S.m[0], S.m[1], p, S.red)) {
+    if (threadIdx.x == 0) {
+      ctrl->done = 3;
+      ctrl->bd_code = 3;
+      if (method == 1) ctrl->iter -= 1;   // cocr forms X_{m+1} only in the last pass
+    }
+    return;
+  }
+  tri_inv_upper(S.m[1], S.m[2], p);
+  gload(S.m[3], slot(mats, M_XI), p);
+  matmul(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
+  gstore(slot(mats, M_XI), S.m[4], p);
+  gstore(slot(mats, M_TAU), S.m[1], p);
+  gstore(slot(mats, M_TINV), S.m[2], p);
+  if (method == 0) {
+    const int E = tri_count(p);
+    expand_tri(S.gs + 2 * E, S.m[0], p, false);       // W^T W
+    matmul(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
+    matmul(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
+    matmul(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
+    gload(S.m[3], slot(mats, M_H), p);                // G_QQ (old)
+    gstore(slot(mats, M_H), S.m[0], p);
+    if (!lu_solve(S.m[3], S.m[4], p, p, S.red, S.ish)) {
+      if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 4; }
+      return;
+    }
+    gstore(slot(mats, M_BETA), S.m[4], p);
+  }
+}
+
+// cocr after V_{m+1} (Algorithm 3, line 8): H+ = T^T (W^T A W) T, beta' = H^{-1} tau^T H+.
+__global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+  SMALL_PROLOGUE
+  if (ctrl->done) return;
+  sum_stage1(stage1, ncomp, S.gs);
+  expand_tri(S.gs, S.m[0], p, false);
+  gload(S.m[1], slot(mats, M_TINV), p);
+  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
+  matmul(S.m[3], S.m[2], false, S.m[1], false, p);   // H+
+  gload(S.m[4], slot(mats, M_TAU), p);
+  matmul(S.m[5], S.m[4], true, S.m[3], false, p);    // tau^T H+
+  gload(S.m[0], slot(mats, M_H), p);
+  gstore(slot(mats, M_H), S.m[3], p);
+  if (!lu_solve(S.m[0], S.m[5], p, p, S.red, S.ish)) {
+    if (threadIdx.x == 0) {
+      ctrl->done = 3;
+      ctrl->bd_code = 4;
+      ctrl->iter -= 1;
+    }
+    return;
+  }
+  gstore(slot(mats, M_BETA), S.m[5], p);
+}
+
+// Norm of the residual from a norm-only residual pass (Sec. 3, true residual).
+__global__ void k_small_trr(int p, const double* stage1, int ncomp, Ctrl* ctrl) {
+  SMALL_PROLOGUE
+  sum_stage1(stage1, ncomp, S.gs);
+  if (threadIdx.x == 0) {
+    const int E = tri_count(p);
+    ctrl->trr = sqrt(S.gs[2 * (2 * E) + 1]);
+    ctrl->sumsq_b = S.gs[2 * (2 * E)];
+  }
+}
+
+// ------------------------------------------------------------------------ CSR checks
+// flags[0]: structure errors, flags[1]: symmetry errors.
+__global__ void k_validate_structure(int64_t n, int64_t nnz, const int* rp, const int* ci, int* flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t b = rp[i], e = rp[i + 1];
+  if (i == 0 && b != 0) atomicAdd(&flags[0], 1);
+  if (i == n - 1 && e != nnz) atomicAdd(&flags[0], 1);
+  if (b < 0 || e < b || e > nnz) {
+    atomicAdd(&flags[0], 1);
+    return;
+  }
+  for (int64_t j = b; j < e; ++j) {
+    const int c = ci[j];
+    if (c < 0 || c >= n || (j > b && c <= ci[j - 1])) {
+      atomicAdd(&flags[0], 1);
+      return;
+    }
+  }
+}
+
+// Requires a structurally valid matrix (checked first).
+__global__ void k_validate_symmetry(int64_t n, const int* rp, const int* ci, const double2* va, double rtol,
+                                    int* flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = rp[i]; j < rp[i + 1]; ++j) {
+    const int c = ci[j];
+    int lo = rp[c], hi = rp[c + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int cm = ci[mid];
+      if (cm == (int)i) { pos = mid; break; }
+      if (cm < (int)i) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    if (pos < 0) {
+      atomicAdd(&flags[1], 1);
+      return;
+    }
+    const double2 x = va[j], y = va[pos];
+    const double d = hypot(x.x - y.x, x.y - y.y);
+    const double s = fmax(hypot(x.x, x.y), hypot(y.x, y.y));
+    if (!(d <= rtol * s)) {
+      atomicAdd(&flags[1], 1);
+      return;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------ host launchers
+static size_t small_smem() { return sizeof(SmallShared); }
+
+static void set_small_attrs() {
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  const int s = (int)small_smem();
+  cudaFuncSetAttribute(k_small_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_cocr_H0, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_cocr_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_trr, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  done[dev] = true;
+}
+
+void prepare_small_kernels() { set_small_attrs(); }
+
+void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s) {
+  const int ncomp = 2 * ne;
+  dim3 grid((ncomp + 31) / 32, RED_SPLIT);
+  k_reduce_stage1<<<grid, 32, 0, s>>>(reinterpret_cast<const double*>(partials), nparts, ncomp, stage1, ctrl);
+}
+
+void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
+                  double* hist, cudaStream_t s) {
+  const size_t sm = small_smem();
+  const int ncomp = 2 * ne;
+  switch (kind) {
+    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl); break;
+    case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
+    case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist); break;
+    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl); break;
+    case SK_COCR_BETA: k_small_cocr_beta<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
+    case SK_TRR: k_small_trr<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, ctrl); break;
+  }
+}
+
+void launch_validate(int64_t n, int64_t nnz, const int* rp, const int* ci, const double2* va, int* flags, int which,
+                     cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  if (which == 0) k_validate_structure<<<blocks, threads, 0, s>>>(n, nnz, rp, ci, flags);
+  else k_validate_symmetry<<<blocks, threads, 0, s>>>(n, rp, ci, va, 1e-12, flags);
+}
+
+}  // namespace blcoc

@@ -1,0 +1,17 @@
+// Host launchers of the p x p kernels, the Gram reduction and the CSR checks.
+#pragma once
+#include "blcoc_common.cuh"
+
+namespace blcoc {
+
+enum SmallKind { SK_SETUP = 0, SK_COCR_H0, SK_ALPHA, SK_CHOL, SK_COCR_BETA, SK_TRR };
+
+void prepare_small_kernels();
+// ctrl == nullptr: run even after the solve has finished (final residual pass).
+void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s);
+void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
+                  double* hist, cudaStream_t s);
+void launch_validate(int64_t n, int64_t nnz, const int* rp, const int* ci, const double2* va, int* flags, int which,
+                     cudaStream_t s);
+
+}  // namespace blcoc

@@ -1,0 +1,5 @@
+// Instantiation of the row-pass kernels for block width 16.
+#include "blcoc_rowpass.cuh"
+namespace blcoc {
+template const KernelSet& kernel_set<16>();
+}

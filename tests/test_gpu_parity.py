@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+* residual history ||xi_m||_F/||B||_F: <= 1e-8 relative for m <= 20;
+* X_m at a fixed iteration count: <= 1e-10 relative (well-conditioned inputs);
+* xi_m elementwise: <= 1e-8 relative to ||xi_m||_F;
+* the sparse product A X: <= 1e-14 relative (single rounding-order difference).
+"""
+import numpy as np
+import pytest
+
+import oracle.blcoc_oracle as O
+from paper_1601_05362_gb300 import problems as P
+from gpu_common import need_gpu, to_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+HIST_TOL = 1e-8
+X_TOL = 1e-10
+
+
+def _handle(A):
+    from paper_1601_05362_gb300 import blcoc
+    return blcoc.Handle.from_csr(A)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 8, 13, 16, 17, 32])
+def test_spmm_matches_scipy(p):
+    torch = need_gpu()
+    A = P.random_complex_symmetric(1000 + p, 9, seed=p)
+    Xh = P.complex_normal(A.n, p, 7)
+    h = _handle(A)
+    X = to_dev(torch, Xh)
+    Y = torch.zeros_like(X)
+    h.spmm(X, Y)
+    Yref = A.to_scipy() @ Xh
+    assert rel(Y.cpu().numpy(), Yref) < 1e-14
+
+
+def test_residual_norm():
+    torch = need_gpu()
+    A = P.helmholtz_2d(37, 5.0, 0.05)
+    B = P.complex_normal(A.n, 6, 1)
+    Xh = P.complex_normal(A.n, 6, 2)
+    h = _handle(A)
+    r = h.residual_norm(to_dev(torch, B), to_dev(torch, Xh))
+    ref = np.linalg.norm(B - A.to_scipy() @ Xh)
+    assert abs(r - ref) <= 1e-13 * ref
+
+
+@pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
+def test_helmholtz2d_n1024_p4_full_solve(method):
+    """The 32x32 2D Helmholtz problem (n=1024, p=4, tol 1e-10, maxit 500)."""
+    torch = need_gpu()
+    pr = P.helmholtz2d_n1024_p4(method)
+    A = pr.A.to_scipy()
+    f = O.bl_cocg_rq if method == "cocg_rq" else O.bl_cocr_rq
+    ref = f(A, pr.B, tol=pr.tol, maxit=pr.maxit)
+    h = _handle(pr.A)
+    B = to_dev(torch, pr.B)
+    X = torch.zeros_like(B)
+    st = h.solve(B, X, method=method, tol=pr.tol, maxit=pr.maxit)
+    info = h.info()
+    assert st == 0, h.last_error()
+    # the residual of this indefinite problem is erratic, so where it first crosses tol
+    # moves by a few iterations under different rounding (BLAS, reduction order)
+    assert abs(info["iters"] - ref.iters) <= max(3, ref.iters // 20)
+    hist = info["hist"]
+    m = min(21, len(hist), len(ref.hist))
+    assert np.max(np.abs(hist[:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m])) < HIST_TOL
+    assert info["relres_true"] <= 10 * pr.tol
+    assert abs(info["relres_true"] - O.true_relres(A, pr.B, X.cpu().numpy())) < 1e-12
+    if info["iters"] == ref.iters:
+        assert rel(X.cpu().numpy(), ref.X) < 1e-8
+
+
+@pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 7, 8, 16, 32])
+def test_fixed_iterations_match_oracle(method, p):
+    """X_m, xi_m and the history after exactly m iterations (tol = 0), ragged n and p."""
+    torch = need_gpu()
+    n = 1500 + 3 * p  # not a multiple of the 32-row chunk
+    A = P.random_complex_symmetric(n, 8, seed=100 + p, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(n, p, 200 + p)
+    X0 = 0.1 * P.complex_normal(n, p, 300 + p)
+    m = 12
+    f = O.bl_cocg_rq if method == "cocg_rq" else O.bl_cocr_rq
+    ref = f(A.to_scipy(), Bh, X0=X0, tol=0.0, maxit=m)
+    h = _handle(A)
+    B = to_dev(torch, Bh)
+    X = to_dev(torch, X0)
+    st = h.solve(B, X, method=method, tol=0.0, maxit=m)
+    info = h.info()
+    assert st == 5, h.last_error()          # not converged: ran exactly m iterations
+    assert info["iters"] == m
+    hist = info["hist"]
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
+    assert rel(X.cpu().numpy(), ref.X) < X_TOL
+    xi = h.xi(p)
+    assert np.max(np.abs(xi - ref.xi)) / np.linalg.norm(ref.xi) < HIST_TOL
+
+
+@pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
+def test_host_pointers_equal_device_pointers(method):
+    torch = need_gpu()
+    pr = P.helmholtz2d_n1024_p4(method)
+    h = _handle(pr.A)
+    Xh = np.zeros_like(pr.B)
+    st = h.solve(pr.B, Xh, method=method, tol=1e-10, maxit=500)
+    info_h = h.info()
+    B = to_dev(torch, pr.B)
+    X = torch.zeros_like(B)
+    st2 = h.solve(B, X, method=method, tol=1e-10, maxit=500)
+    assert st == st2 == 0
+    assert np.array_equal(Xh, X.cpu().numpy())          # bitwise: deterministic reductions
+    assert info_h["iters"] == h.info()["iters"]
+
+
+def test_graph_and_direct_launches_agree_bitwise():
+    torch = need_gpu()
+    pr = P.helmholtz2d_n1024_p4("cocr_rq")
+    h = _handle(pr.A)
+    B = to_dev(torch, pr.B)
+    out = []
+    for g, poll in ((1, 16), (0, 16), (1, 5)):
+        h.set_option("graph", g)
+        h.set_option("poll", poll)
+        X = torch.zeros_like(B)
+        assert h.solve(B, X, tol=1e-10, maxit=500) == 0
+        out.append((X.cpu().numpy(), h.info()["iters"]))
+    for X, it in out[1:]:
+        assert it == out[0][1] and np.array_equal(X, out[0][0])
+
+
+def test_edge_cases():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    A = P.random_complex_symmetric(300, 6, seed=1)
+    h = _handle(A)
+    Bh = P.complex_normal(300, 3, 1)
+    B = to_dev(torch, Bh)
+    # maxit = 0: X unchanged, not converged
+    X0 = to_dev(torch, P.complex_normal(300, 3, 2))
+    X = X0.clone()
+    assert h.solve(B, X, tol=1e-10, maxit=0) == blcoc.BLCOC_NOT_CONVERGED
+    assert torch.equal(X, X0) and h.info()["iters"] == 0
+    # zero right-hand side: X = 0, converged at once
+    Z = torch.zeros_like(B)
+    X = X0.clone()
+    assert h.solve(Z, X, tol=1e-10, maxit=10) == 0
+    assert float(X.abs().max()) == 0.0
+    # exact initial guess converges at iteration 0
+    Xs = np.linalg.solve(A.to_dense(), Bh)
+    X = to_dev(torch, Xs)
+    assert h.solve(B, X, tol=1e-8, maxit=10) == 0 and h.info()["iters"] == 0
+    # duplicated columns: the residual block has no full rank -> breakdown
+    Bd = Bh.copy()
+    Bd[:, 1] = Bd[:, 0]
+    X = torch.zeros_like(B)
+    assert h.solve(to_dev(torch, Bd), X, tol=1e-10, maxit=50) == blcoc.BLCOC_BREAKDOWN
+    # invalid arguments
+    with pytest.raises(blcoc.BlcocError):
+        h.solve(B, torch.zeros_like(B), tol=-1.0)
+    st = h._lib.blcoc_solve(h._h, B.data_ptr(), X.data_ptr(), 33, 1, 1e-10, 10)
+    assert st == blcoc.BLCOC_ERR_INVALID_ARG
+    st = h._lib.blcoc_solve(h._h, B.data_ptr(), X.data_ptr(), 3, 7, 1e-10, 10)
+    assert st == blcoc.BLCOC_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_matrices():
+    need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    A = P.random_complex_symmetric(200, 6, seed=3)
+    v = A.vals.copy()
+    v[5] += 0.5  # breaks a_ij = a_ji
+    with pytest.raises(blcoc.BlcocError) as e:
+        blcoc.Handle(A.n, A.row_ptr, A.col_idx, v)
+    assert e.value.status == blcoc.BLCOC_ERR_NOT_SYMMETRIC
+    ci = A.col_idx.copy()
+    ci[3] = A.n + 5  # out of range column
+    with pytest.raises(blcoc.BlcocError) as e:
+        blcoc.Handle(A.n, A.row_ptr, ci, A.vals)
+    assert e.value.status == blcoc.BLCOC_ERR_INVALID_ARG
+    rp = A.row_ptr.copy()
+    rp[10], rp[11] = rp[11], rp[10]  # non-monotone row pointers
+    with pytest.raises(blcoc.BlcocError) as e:
+        blcoc.Handle(A.n, rp, A.col_idx, A.vals)
+    assert e.value.status == blcoc.BLCOC_ERR_INVALID_ARG
+
+
+def test_device_csr_input():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    A = P.helmholtz_2d(20, 4.0, 0.05)
+    h = blcoc.Handle(A.n, to_dev(torch, A.row_ptr), to_dev(torch, A.col_idx), to_dev(torch, A.vals))
+    Xh = P.complex_normal(A.n, 2, 0)
+    X = to_dev(torch, Xh)
+    Y = torch.zeros_like(X)
+    h.spmm(X, Y)
+    assert rel(Y.cpu().numpy(), A.to_scipy() @ Xh) < 1e-14
