@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--method", choices=["cocr_rq", "cocg_rq"], default="cocr_rq")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
+                    help="profiler case: one solve of the same workload for exactly ITERS iterations, then exit")
     return ap.parse_args()
 
 
@@ -357,8 +359,27 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_ncu_case(args):
+    """A short, fixed-length solve of the bench workload for ncu captures (no timing)."""
+    import torch
+    from paper_1601_05362_gb300 import blcoc, build
+    build.build()
+    pr = problem(args.method)
+    h = blcoc.Handle.from_csr(pr.A)
+    B = torch.from_numpy(pr.B).cuda()
+    X = torch.zeros_like(B)
+    st = h.solve(B, X, method=args.method, tol=0.0, maxit=args.ncu_case)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case_iters": args.ncu_case, "status": blcoc.status_string(st),
+                      "launches": h.stat("launches")}))
+    h.close()
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     if args.cpu_sample:
         cpu_sample(args.method, args.cpu_sample)
         return
