@@ -139,6 +139,34 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
  * cocr_passC, cocg_pass1, cocg_pass2. */
 blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value);
 
+/*
+ * blcoc_residual_norm_noalloc - ||B - A X||_F, allocating no device memory.
+ *
+ * For callers that cannot call cudaMalloc (for example code running while a memory
+ * pool or caching allocator is held by its owner, or inside another library's
+ * allocation-free section): it takes no handle, because creating one allocates.  The
+ * paper has no counterpart; the value is the same true residual as
+ * blcoc_residual_norm (up to summation order).
+ *   n, row_ptr, col_idx, vals : CSR of A in device memory (same layout as blcoc_create;
+ *                               not checked here: pass a matrix that blcoc_create accepts).
+ *   B, X       : n x p device blocks, 1 <= p <= BLCOC_MAX_P, n < 2^31.
+ *   norm_out   : device pointer; receives ||B - A X||_F in norm_out[0].
+ *   cuda_stream: stream the two kernels are queued on (NULL = legacy default); the call
+ *                returns without waiting for them.
+ * Scratch: a static device array of BLCOC_NOALLOC_MAX_CTAS x 2 doubles (16 KB) that every
+ * GPU loading the library holds until exit; the row pass uses at most that many CTAs, so
+ * any n fits.  Each call overwrites the slots it reads; calls that overlap on the GPU
+ * (other streams, other threads) race on the shared array.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.
+ * Errors: BLCOC_ERR_INVALID_ARG for n or p out of range or a NULL pointer (message in
+ * blcoc_last_error(NULL)), BLCOC_ERR_CUDA if the set-up or a launch fails.
+ */
+#define BLCOC_NOALLOC_MAX_CTAS 1024
+blcoc_status blcoc_residual_norm_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                         const void* vals, const void* B, const void* X, int p,
+                                         double* norm_out, void* cuda_stream);
+
 /* blcoc_destroy - free the handle and everything it owns.  NULL is accepted. */
 blcoc_status blcoc_destroy(blcoc_handle h);
 

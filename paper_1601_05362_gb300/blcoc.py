@@ -41,6 +41,8 @@ SIGNATURES = {
     "blcoc_residual_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "blcoc_set_option": (C.c_int, [C.c_void_p, C.c_char_p, C.c_int64]),
     "blcoc_get_stat": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int64)]),
+    "blcoc_residual_norm_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "blcoc_destroy": (C.c_int, [C.c_void_p]),
     "blcoc_status_string": (C.c_char_p, [C.c_int]),
     "blcoc_last_error": (C.c_char_p, [C.c_void_p]),

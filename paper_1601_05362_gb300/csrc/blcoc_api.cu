@@ -24,6 +24,12 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+void blcoc::set_global_error(const char* msg) { g_create_error = msg; }
+
+namespace {
+
 const KernelSet* kernels_for(int p, int* PP) {
   if (p <= 1) { *PP = 1; return &kernel_set<1>(); }
   if (p <= 2) { *PP = 2; return &kernel_set<2>(); }

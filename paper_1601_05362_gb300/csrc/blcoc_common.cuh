@@ -116,4 +116,7 @@ struct KernelSet {
 
 template <int PP> const KernelSet& kernel_set();
 
+// Sets the message blcoc_last_error(NULL) returns (calling thread only).
+void set_global_error(const char* msg);
+
 }  // namespace blcoc
