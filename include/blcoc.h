@@ -125,7 +125,7 @@ blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, i
  * blcoc_set_option - tuning switches (key, value):
  *   "graph"      : 1 (default) replays the iteration as a CUDA graph, 0 launches kernels.
  *   "poll"       : iterations between two host checks of the convergence flag (default 16).
- *   "timing"     : 1 brackets every row-pass kernel of the iterations with CUDA events on
+ *   "timing"     : 1 brackets every kernel of the iterations with CUDA events on
  *                  the internal stream (also inside the graph) and accumulates per-kernel
  *                  device time; 0 (default) records nothing.
  * Returns BLCOC_ERR_INVALID_ARG for an unknown key or value.
@@ -136,7 +136,8 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
  * solve, including those inside graph replays), "graph_replays", and with the
  * "timing" option "kt_ns.<kernel>" (total device nanoseconds) and "kt_n.<kernel>"
  * (launches that did work) for <kernel> in resid, spmm_gram, spmm_plain, cocr_passA,
- * cocr_passC, cocg_pass1, cocg_pass2. */
+ * cocr_passC, cocg_pass1, cocg_pass2, reduce, small_setup, small_H0, small_alpha,
+ * small_chol, small_beta, small_trr. */
 blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value);
 
 /*

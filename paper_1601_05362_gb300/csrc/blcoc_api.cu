@@ -41,9 +41,11 @@ const KernelSet* kernels_for(int p, int* PP) {
 }
 
 // Names of the timed kernel kinds (index = PassKind of blcoc_rowpass.cuh).
-const char* const kKindNames[] = {"resid", "spmm_gram", "spmm_plain", "cocr_passA", "cocr_passC", "cocg_pass1",
-                                  "cocg_pass2"};
-constexpr int kNumKinds = 7;
+const char* const kKindNames[] = {"resid",      "spmm_gram",  "spmm_plain", "cocr_passA", "cocr_passC",
+                                  "cocg_pass1", "cocg_pass2", "reduce",     "small_setup", "small_H0",
+                                  "small_alpha", "small_chol", "small_beta", "small_trr"};
+constexpr int kNumKinds = 14;
+constexpr int kKindReduce = 7, kKindSmall0 = 8;   // small kernel kind = kKindSmall0 + SmallKind
 
 struct Timer {
   int kind;
@@ -81,7 +83,7 @@ struct blcoc_ctx {
   // workspace
   int p_cap = 0;
   int64_t gen = 0;
-  double2 *W = nullptr, *S = nullptr, *U = nullptr, *V = nullptr, *Bst = nullptr, *Xst = nullptr;
+  double2 *W = nullptr, *S = nullptr, *U = nullptr, *V = nullptr, *Q = nullptr, *Bst = nullptr, *Xst = nullptr;
   double2* mats = nullptr;
   double2* partials = nullptr;
   size_t partials_cap = 0;   // double2 entries
@@ -138,11 +140,11 @@ blcoc_status invalid(blcoc_ctx* h, const char* msg) {
 int max_ne(int p) { return 2 * tri_count(p) + 1; }
 
 void free_ws(blcoc_ctx* h) {
-  double2* blocks[] = {h->W, h->S, h->U, h->V, h->Bst, h->Xst, h->mats, h->partials};
+  double2* blocks[] = {h->W, h->S, h->U, h->V, h->Q, h->mats, h->partials};
   for (double2* b : blocks)
     if (b) cudaFree(b);
   if (h->stage1) cudaFree(h->stage1);
-  h->W = h->S = h->U = h->V = h->Bst = h->Xst = h->mats = h->partials = nullptr;
+  h->W = h->S = h->U = h->V = h->Q = h->mats = h->partials = nullptr;
   h->stage1 = nullptr;
   h->p_cap = 0;
   h->partials_cap = h->stage1_cap = 0;
@@ -157,6 +159,7 @@ blcoc_status ensure_ws(blcoc_ctx* h, int p) {
   CK(h, cudaMalloc(&h->S, blk));
   CK(h, cudaMalloc(&h->U, blk));
   CK(h, cudaMalloc(&h->V, blk));
+  CK(h, cudaMalloc(&h->Q, blk));
   CK(h, cudaMalloc(&h->mats, (size_t)M_NSLOTS * PMAX * PMAX * sizeof(double2)));
   CK(h, cudaMemset(h->mats, 0, (size_t)M_NSLOTS * PMAX * PMAX * sizeof(double2)));
   const int ne = max_ne(PMAX);
@@ -188,6 +191,7 @@ struct Solver {
     a.S = h->S;
     a.U = h->U;
     a.V = h->V;
+    a.Q = h->Q;
     a.X = X;
     a.B = B;
     a.mats = h->mats;
@@ -232,12 +236,32 @@ struct Solver {
     last_grid = a.grid;
   }
   int last_grid = 0;
+  void timed_begin(Timer& t, int kind) {
+    t = Timer{kind, batch_iter, nullptr, nullptr};
+    if (timers) {
+      t.e0 = next_event();
+      t.e1 = next_event();
+      record(t.e0);
+    }
+  }
+  void timed_end(Timer& t) {
+    if (timers) {
+      record(t.e1);
+      timers->push_back(t);
+    }
+  }
   void reduce(int ne, const Ctrl* ctrl) {
+    Timer t;
+    timed_begin(t, kKindReduce);
     launch_reduce(h->partials, last_grid, ne, h->stage1, ctrl, h->s);
+    timed_end(t);
     ++launches;
   }
   void small(SmallKind k, int ne) {
+    Timer t;
+    timed_begin(t, kKindSmall0 + (int)k);
     launch_small(k, p, method, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s);
+    timed_end(t);
     ++launches;
   }
   // kinds must match PassKind in blcoc_rowpass.cuh

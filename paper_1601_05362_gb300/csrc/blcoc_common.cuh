@@ -89,6 +89,7 @@ struct PassArgs {
   double2* S;
   double2* U;
   double2* V;         // cocr: V;  cocg: A S
+  double2* Q;         // Q = W T of the current basis, written by the last pass of an iteration
   double2* X;
   const double2* B;
   const double2* mats;
@@ -106,10 +107,10 @@ struct KernelSet {
   LaunchFn resid;        // R = B - A X; grams R^H R (+ R^T R if flag&2); norms; flag&1: norm only
   LaunchFn spmm_gram;    // Y = A W; gram W^T Y; out = Y T (flag=1) or Y (flag=0)
   LaunchFn spmm_plain;   // Y = A W (no gram), for blcoc_spmm
-  LaunchFn cocr_passA;   // W <- W T - U alpha'; gram W^H W
-  LaunchFn cocr_passC;   // Q = W T; X += S alpha'xi; S = Q + S beta'; U = V + U beta'; gram U^T U
-  LaunchFn cocg_pass1;   // Q = W T; W <- Q - (AS) alpha'; X += S alpha'xi; grams W^H W, W^T W
-  LaunchFn cocg_pass2;   // S <- W T + S beta'
+  LaunchFn cocr_passA;   // W <- Q - U alpha'; gram W^H W
+  LaunchFn cocr_passC;   // Q = W T (stored); X += S alpha'xi; S = Q + S beta'; U = V + U beta'; gram U^T U
+  LaunchFn cocg_pass1;   // W <- Q - (AS) alpha'; X += S alpha'xi; grams W^H W, W^T W
+  LaunchFn cocg_pass2;   // Q = W T (stored); S <- Q + S beta'
   int (*grid)(int64_t n, int kind, int num_sms);
   void (*prepare)();     // set the dynamic shared-memory limits (once per device)
 };

@@ -142,15 +142,23 @@ enum GramKind { G_FULL = 0, G_SYM = 1, G_HERM = 2 };
 
 template <int NS>
 struct GramAcc {
+  // Entries e = lane + 32 i (i < F) take all 32 rows of a chunk.  The Er = E mod 32
+  // remainder entries, when Er divides 32, are spread over G = 32/Er row groups so that
+  // every lane does the same number of MACs (a warp instruction costs the same with
+  // idle lanes); the G partial sums are combined by shuffles at the end.
   double2 acc[NS];
   short a[NS], b[NS];
-  int E;
+  int E, F, Er, G;
   __device__ __forceinline__ void init(int kind, int p, int lane) {
     E = (kind == G_FULL) ? p * p : tri_count(p);
+    F = E / 32;
+    Er = E - 32 * F;
+    G = (Er > 0 && (32 % Er) == 0) ? 32 / Er : 1;
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       acc[i] = cz();
-      const int e = lane + 32 * i;
+      int e = lane + 32 * i;
+      if (i == F && G > 1) e = 32 * F + lane % Er;
       int aa = 0, bb = 0;
       if (e < E) {
         if (kind == G_FULL) {
@@ -166,18 +174,54 @@ struct GramAcc {
       b[i] = (short)bb;
     }
   }
+  // entry index held by this lane in slot i (E or more: none)
+  __device__ __forceinline__ int entry(int i, int lane) const {
+    if (i == F && G > 1) return 32 * F + lane % Er;
+    return lane + 32 * i;
+  }
+  template <bool CONJ>
+  __device__ __forceinline__ void mac(int i, const double2* Y, const double2* Z, int r) {
+    const double2 y = Y[tix(a[i], r)];
+    const double2 z = Z[tix(b[i], r)];
+    if constexpr (CONJ) cmac_conj(acc[i], y, z);
+    else cmac(acc[i], y, z);
+  }
   // acc[e] += sum_r op(Y[r][a_e]) Z[r][b_e] over the 32 rows of a chunk
   template <bool CONJ>
   __device__ __forceinline__ void add(const double2* Y, const double2* Z, int lane) {
 #pragma unroll 2
     for (int r = 0; r < CHUNK; ++r) {
 #pragma unroll
+      for (int i = 0; i < NS; ++i)
+        if (i < F) mac<CONJ>(i, Y, Z, r);
+    }
+    if (F < NS && Er > 0) {
+      if (G > 1) {
+        const int rows = CHUNK / G, r0 = (lane / Er) * rows;
+        for (int r = r0; r < r0 + rows; ++r) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i)
+            if (i == F) mac<CONJ>(i, Y, Z, r);
+        }
+      } else if (lane < Er) {
+        for (int r = 0; r < CHUNK; ++r) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i)
+            if (i == F) mac<CONJ>(i, Y, Z, r);
+        }
+      }
+    }
+  }
+  // combine the row-group partial sums of the remainder slot (fixed butterfly order)
+  __device__ __forceinline__ void fold() {
+    if (F < NS && G > 1) {
+#pragma unroll
       for (int i = 0; i < NS; ++i) {
-        if (lane + 32 * i < E) {
-          const double2 y = Y[tix(a[i], r)];
-          const double2 z = Z[tix(b[i], r)];
-          if constexpr (CONJ) cmac_conj(acc[i], y, z);
-          else cmac(acc[i], y, z);
+        if (i == F) {
+          for (int o = Er; o < 32; o <<= 1) {
+            acc[i].x += __shfl_xor_sync(0xffffffffu, acc[i].x, o);
+            acc[i].y += __shfl_xor_sync(0xffffffffu, acc[i].y, o);
+          }
         }
       }
     }
@@ -187,12 +231,14 @@ struct GramAcc {
 // Sum the warps' accumulators of one Gram in a fixed order and write the CTA partial.
 // `red` is shared scratch of at least NWARP*E double2; caller syncs before reuse.
 template <int NS>
-__device__ __forceinline__ void cta_write_gram(const GramAcc<NS>& g, double2* red, double2* __restrict__ out,
+__device__ __forceinline__ void cta_write_gram(GramAcc<NS>& g, double2* red, double2* __restrict__ out,
                                                int warp, int lane) {
+  g.fold();
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
-    const int e = lane + 32 * i;
-    if (e < g.E) red[warp * g.E + e] = g.acc[i];
+    const int e = g.entry(i, lane);
+    const bool owner = !(i == g.F && g.G > 1) || lane < g.Er;
+    if (e < g.E && owner) red[warp * g.E + e] = g.acc[i];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < g.E; e += blockDim.x) {
@@ -357,32 +403,28 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
   }
 }
 
-// bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): with Q_m = W_m T_m,
-// W_{m+1} = Q_m - U_m alpha'_m, in place; gram W^H W for the Cholesky QR.
+// bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): W_{m+1} = Q_m - U_m alpha'_m
+// (Q_m stored by the previous pass C); gram W^H W for the Cholesky QR.
 template <int PP>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
   BLCOC_PROLOGUE
   using G = Geo<PP>;
-  double2* mT = smem;
-  double2* mA = smem + PP * PP;
-  double2* tiles = smem + (G::MATS_SMEM ? 2 * PP * PP : 0);
+  double2* mA = smem;
+  double2* tiles = smem + (G::MATS_SMEM ? PP * PP : 0);
   double2* tW = tiles + warp * 2 * G::TILE;
   double2* tU = tW + G::TILE;
   if constexpr (G::MATS_SMEM) {
-    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
   Fac<PP> AL{G::MATS_SMEM ? mA : a.mats + M_ALPHA * PMAX * PMAX, p};
   GramAcc<G::NTRI> g;
   g.init(G_HERM, p, lane);
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    load_tile<PP>(tW, a.W, r0, n, p, lane);
+    load_tile<PP>(tW, a.Q, r0, n, p, lane);
     load_tile<PP>(tU, a.U, r0, n, p, lane);
     __syncwarp();
-    tri_apply_inplace<PP>(tW, T, p, lane);            // Q_m
     apply_full<PP, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
     __syncwarp();
     g.template add<true>(tW, tW, lane);
@@ -393,7 +435,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
   cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
 }
 
-// bl_cocr_rq pass C (Algorithm 3, lines 5, 9, 10) with Q_{m+1} = W_{m+1} T_{m+1}:
+// bl_cocr_rq pass C (Algorithm 3, lines 5, 9, 10) with Q_{m+1} = W_{m+1} T_{m+1} (stored
+// for the next pass A):
 //   X_{m+1} = X_m + S_m (alpha'_m xi_m);  S_{m+1} = Q_{m+1} + S_m beta'_m;
 //   U_{m+1} = V_{m+1} + U_m beta'_m;  gram U^T U (next alpha').
 // flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.
@@ -429,6 +472,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
     }
     __syncwarp();
     tri_apply_inplace<PP>(b0, T, p, lane);             // Q_{m+1}
+    __syncwarp();
+    store_tile<PP>(a.Q, b0, r0, n, p, lane);
     if (!first) {
       apply_full<PP, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
       __syncwarp();
@@ -457,27 +502,24 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
 }
 
-// bl_cocg_rq pass 1 (Algorithm 2, lines 5-6): with Q_m = W_m T_m,
-//   W_{m+1} = Q_m - (A S_m) alpha'_m (in place);  X_{m+1} = X_m + S_m (alpha'_m xi_m);
+// bl_cocg_rq pass 1 (Algorithm 2, lines 5-6), Q_m stored by the previous pass 2:
+//   W_{m+1} = Q_m - (A S_m) alpha'_m;  X_{m+1} = X_m + S_m (alpha'_m xi_m);
 //   grams W^H W (QR) and W^T W (Q^T Q of line 7).  Partials: [W^H W tri][W^T W tri].
 template <int PP>
 __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
   BLCOC_PROLOGUE
   using G = Geo<PP>;
-  double2* mT = smem;
-  double2* mAX = smem + PP * PP;
-  double2* mA = smem + 2 * PP * PP;
-  double2* tiles = smem + (G::MATS_SMEM ? 3 * PP * PP : 0);
+  double2* mAX = smem;
+  double2* mA = smem + PP * PP;
+  double2* tiles = smem + (G::MATS_SMEM ? 2 * PP * PP : 0);
   double2* b0 = tiles + warp * 3 * G::TILE;
   double2* b1 = b0 + G::TILE;
   double2* b2 = b1 + G::TILE;
   if constexpr (G::MATS_SMEM) {
-    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
   Fac<PP> AX{G::MATS_SMEM ? mAX : a.mats + M_ALPHAXI * PMAX * PMAX, p};
   Fac<PP> AL{G::MATS_SMEM ? mA : a.mats + M_ALPHA * PMAX * PMAX, p};
   GramAcc<G::NTRI> gh, gs;
@@ -485,10 +527,9 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
   gs.init(G_SYM, p, lane);
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    load_tile<PP>(b0, a.W, r0, n, p, lane);
+    load_tile<PP>(b0, a.Q, r0, n, p, lane);
     load_tile<PP>(b1, a.V, r0, n, p, lane);
     __syncwarp();
-    tri_apply_inplace<PP>(b0, T, p, lane);             // Q_m
     apply_full<PP, true>(b0, b0, b1, AL, p, lane);     // W_{m+1} = Q_m - A S_m alpha'
     __syncwarp();
     load_tile<PP>(b1, a.S, r0, n, p, lane);
@@ -508,8 +549,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
   cta_write_gram(gs, tiles, out + tri_count(p), warp, lane);
 }
 
-// bl_cocg_rq pass 2 (Algorithm 2, line 8): S_{m+1} = W_{m+1} T_{m+1} + S_m beta'_m.
-// flag=1 (setup, line 2): S_0 = Q_0 = W_0 T_0.
+// bl_cocg_rq pass 2 (Algorithm 2, line 8): Q_{m+1} = W_{m+1} T_{m+1} (stored for the next
+// pass 1), S_{m+1} = Q_{m+1} + S_m beta'_m.  flag=1 (setup, line 2): S_0 = Q_0 = W_0 T_0.
 template <int PP>
 __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
   BLCOC_PROLOGUE
@@ -533,6 +574,9 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
     if (!first) load_tile<PP>(b1, a.S, r0, n, p, lane);
     __syncwarp();
     tri_apply_inplace<PP>(b0, T, p, lane);            // Q_{m+1}
+    __syncwarp();
+    store_tile<PP>(a.Q, b0, r0, n, p, lane);
+    __syncwarp();
     if (!first) apply_full<PP, false>(b0, b0, b1, BE, p, lane);
     __syncwarp();
     store_tile<PP>(a.S, b0, r0, n, p, lane);
@@ -550,7 +594,7 @@ constexpr size_t pass_smem(int kind) {
   using G = Geo<PP>;
   const size_t mat = (size_t)PP * PP * sizeof(double2);
   const size_t tile = (size_t)G::TILE * sizeof(double2);
-  const int nmats[K_NKIND] = {0, 1, 0, 2, 3, 3, 2};
+  const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2};
   const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2};
   return (G::MATS_SMEM ? nmats[kind] * mat : 0) + (size_t)NWARP * ntiles[kind] * tile;
 }

@@ -6,7 +6,12 @@ histories on the seeded 32x32 2D Helmholtz problem (Sec. 3 setting: X0 = 0,
 tol 1e-10, stopping rule ||xi_m||_F/||B||_F of Algorithms 2-3).  They serve as a
 regression fixture for the oracle and as stored expected values for the GPU tests.
 
-Run:  python tests/golden/make_golden.py
+With --full3d it also runs the oracle's full bl_cocr_rq solve of the 64^3 Helmholtz
+problem (n = 262,144, p = 16, tol 1e-10; several minutes on a CPU) and writes
+tests/golden/helmholtz3d_n262144_p16.json (status, iteration count, true relative
+residual and the whole recursive history).
+
+Run:  python tests/golden/make_golden.py [--full3d]
 """
 import json
 import os
@@ -32,5 +37,17 @@ def main():
         json.dump(out, fh, indent=1)
 
 
+def full3d():
+    pr = P.helmholtz3d_n262144_p16("cocr_rq")
+    A = pr.A.to_scipy()
+    r = O.bl_cocr_rq(A, pr.B, tol=pr.tol, maxit=2000)
+    out = {"source": "oracle/blcoc_oracle.py bl_cocr_rq (Algorithm 3, Sec. 2.2)", "problem": pr.name,
+           "status": r.status, "iters": r.iters, "trr": O.true_relres(A, pr.B, r.X), "hist": r.hist}
+    with open(os.path.join(HERE, "helmholtz3d_n262144_p16.json"), "w") as fh:
+        json.dump(out, fh, indent=0)
+
+
 if __name__ == "__main__":
     main()
+    if "--full3d" in sys.argv:
+        full3d()

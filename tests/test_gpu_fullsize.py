@@ -1,0 +1,81 @@
+"""Parity at the bench size: the 64^3 Helmholtz problem (n = 262,144, p = 16) solved by
+bl_cocr_rq in the launch configuration bench.py times (CUDA graph, poll 16).
+
+* the first iterations against the oracle run here: history <= 1e-8 for m <= 20;
+  X_5 <= 1e-10; X_20 within 10x the oracle's own sensitivity to a rounding-level (1e-16)
+  perturbation of B (about 7.5e-9 at this size: the iterates of this indefinite problem
+  amplify rounding differences, so the benchmark spec's 1e-10 on X holds early but not at m = 20
+  for any two FP64 implementations);
+* the full solve against properties that hold at any size and against the oracle's own
+  full solve stored in tests/golden/helmholtz3d_n262144_p16.json (written by
+  tests/golden/make_golden.py --full3d): the reported true residual equals a CPU
+  recomputation, it is within the attainable accuracy the oracle itself reaches on this
+  problem, and the iteration count is close to the oracle's.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle.blcoc_oracle as O
+from paper_1601_05362_gb300 import problems as P
+from gpu_common import need_gpu, to_dev, rel
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "helmholtz3d_n262144_p16.json")
+
+
+@pytest.fixture(scope="module")
+def problem():
+    return P.helmholtz3d_n262144_p16("cocr_rq")
+
+
+def test_first_iterations_match_oracle(problem):
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    pr = problem
+    A = pr.A.to_scipy()
+    ref5 = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=5)
+    ref = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=20)
+    Bp = pr.B * (1.0 + 1e-16 * np.random.default_rng(0).standard_normal(pr.B.shape))
+    sens = rel(O.bl_cocr_rq(A, Bp, tol=0.0, maxit=20).X, ref.X)
+    out = {}
+    with blcoc.Handle.from_csr(pr.A) as h:
+        B = to_dev(torch, pr.B)
+        for m in (5, 20):
+            X = torch.zeros_like(B)
+            assert h.solve(B, X, tol=0.0, maxit=m) == blcoc.BLCOC_NOT_CONVERGED
+            out[m] = (X.cpu().numpy(), h.info(), h.xi(pr.p))
+    X5, _, _ = out[5]
+    X20, info, xi = out[20]
+    hist = np.asarray(info["hist"])
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8
+    assert rel(X5, ref5.X) < 1e-10
+    assert rel(X20, ref.X) < max(1e-10, 10 * sens), (rel(X20, ref.X), sens)
+    assert np.max(np.abs(xi - ref.xi)) / np.linalg.norm(ref.xi) < 1e-8
+
+
+def test_full_solve_properties(problem):
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    pr = problem
+    with blcoc.Handle.from_csr(pr.A) as h:
+        B = to_dev(torch, pr.B)
+        X = torch.zeros_like(B)
+        st = h.solve(B, X, tol=pr.tol, maxit=pr.maxit)
+        info = h.info()
+    assert st == blcoc.BLCOC_OK
+    assert info["relres"] <= pr.tol and info["hist"][-1] <= pr.tol
+    trr_cpu = O.true_relres(pr.A.to_scipy(), pr.B, X.cpu().numpy())
+    assert abs(info["relres_true"] - trr_cpu) <= 1e-6 * trr_cpu
+    if os.path.exists(GOLDEN):
+        g = json.load(open(GOLDEN))
+        assert g["status"] == "converged"
+        # the oracle reaches a true residual of about 1.6e-8 here (growth of the
+        # residual to ~16x before convergence limits the attainable accuracy)
+        assert trr_cpu <= 5 * g["trr"]
+        assert abs(info["iters"] - g["iters"]) <= 0.15 * g["iters"]
+    else:
+        assert trr_cpu <= 1e-7
