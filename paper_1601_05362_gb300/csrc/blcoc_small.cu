@@ -32,19 +32,71 @@ __global__ void k_reduce_stage1(const double* __restrict__ partials, int nparts,
   if (c >= ncomp) return;
   const int s = blockIdx.y;
   const int q0 = (int)((int64_t)s * nparts / RED_SPLIT), q1 = (int)((int64_t)(s + 1) * nparts / RED_SPLIT);
-  double acc = 0.0;
-  for (int q = q0; q < q1; ++q) acc += partials[(int64_t)q * ncomp + c];
-  stage1[(int64_t)s * ncomp + c] = acc;
+  // four interleaved accumulators: the loads are independent and the add chains short
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int q = q0;
+  for (; q + 4 <= q1; q += 4) {
+    const double v0 = partials[(int64_t)q * ncomp + c], v1 = partials[(int64_t)(q + 1) * ncomp + c];
+    const double v2 = partials[(int64_t)(q + 2) * ncomp + c], v3 = partials[(int64_t)(q + 3) * ncomp + c];
+    a0 += v0;
+    a1 += v1;
+    a2 += v2;
+    a3 += v3;
+  }
+  for (; q < q1; ++q) a0 += partials[(int64_t)q * ncomp + c];
+  stage1[(int64_t)s * ncomp + c] = (a0 + a1) + (a2 + a3);
 }
 
 // Second stage, inside the small kernels: gs[c] = sum_s stage1[s][c].
 __device__ void sum_stage1(const double* __restrict__ stage1, int ncomp, double* gs) {
+  static_assert(RED_SPLIT % 4 == 0, "stage-1 slices are summed four at a time");
   for (int c = threadIdx.x; c < ncomp; c += blockDim.x) {
-    double acc = 0.0;
-    for (int s = 0; s < RED_SPLIT; ++s) acc += stage1[(int64_t)s * ncomp + c];
-    gs[c] = acc;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int s = 0; s < RED_SPLIT; ++s) a[s & 3] += stage1[(int64_t)s * ncomp + c];
+    gs[c] = (a[0] + a[1]) + (a[2] + a[3]);
   }
   __syncthreads();
+}
+
+// Deterministic CTA-wide sum (butterfly within warps, then over the warps' results).
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (lane == 0) red[32] = w;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// Reciprocal of a positive finite double by Newton's iteration r <- r (2 - d r) from a
+// single-precision start (two steps: ~48 correct bits -> within 1 ulp).  Used where a
+// division would sit on a long sequential chain (pivots of the p x p factorisations).
+// d = m 2^e is split with integer operations so that the float start never leaves the
+// float range; exponents near the ends of the double range fall back to a division.
+__device__ __forceinline__ double recip_pos(double d) {
+  const long long bits = __double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7FF) - 1023;
+  if (ex < -1000 || ex > 1000) return 1.0 / d;
+  const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);  // [1, 2)
+  double r = (double)__frcp_rn((float)m);
+  double e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  return r * __longlong_as_double((long long)(1023 - ex) << 52);   // exact scaling by 2^-ex
+}
+__device__ __forceinline__ double2 crecip_fast(double2 z) {
+  const double d = fma(z.x, z.x, z.y * z.y);
+  const double r = recip_pos(d);
+  return make_double2(z.x * r, -z.y * r);
 }
 
 __device__ __forceinline__ void tri_decode(int e, int p, int& a, int& b) {
@@ -80,13 +132,14 @@ __device__ void gstore(double2* __restrict__ g, const double2* s, int p) {
 __device__ void matmul(double2* C, const double2* A, bool tA, const double2* B, bool tB, int p) {
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e / p, j = e % p;
-    double2 acc = cz();
-    for (int k = 0; k < p; ++k) {
-      const double2 a = tA ? A[k * LD + i] : A[i * LD + k];
-      const double2 b = tB ? B[j * LD + k] : B[k * LD + j];
-      cmac(acc, a, b);
+    double2 acc0 = cz(), acc1 = cz();
+    int k = 0;
+    for (; k + 2 <= p; k += 2) {
+      cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
+      cmac(acc1, tA ? A[(k + 1) * LD + i] : A[i * LD + k + 1], tB ? B[j * LD + k + 1] : B[(k + 1) * LD + j]);
     }
-    C[i * LD + j] = acc;
+    if (k < p) cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
+    C[i * LD + j] = make_double2(acc0.x + acc1.x, acc0.y + acc1.y);
   }
   __syncthreads();
 }
@@ -97,17 +150,7 @@ __device__ double fro_norm(const double2* M, int p, double* red) {
     const double2 v = M[(e / p) * LD + e % p];
     acc += v.x * v.x + v.y * v.y;
   }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int t = 0; t < (int)blockDim.x; ++t) s += red[t];
-    red[0] = sqrt(s);
-  }
-  __syncthreads();
-  const double r = red[0];
-  __syncthreads();
-  return r;
+  return sqrt(block_sum(acc, red));
 }
 
 // Right-looking Cholesky of a Hermitian G (upper triangle used, destroyed): tau^H tau = G.
@@ -120,9 +163,9 @@ __device__ bool chol_upper(double2* G, double2* tau, int p, double* sh) {
       if (!(d > 0.0) || !isfinite(d)) {
         sh[0] = 0.0;
       } else {
-        const double r = sqrt(d);
-        tau[j * LD + j] = make_double2(r, 0.0);
-        sh[0] = 1.0 / r;
+        const double ir = rsqrt(d);
+        tau[j * LD + j] = make_double2(d * ir, 0.0);
+        sh[0] = ir;
       }
     }
     __syncthreads();
@@ -151,45 +194,55 @@ __device__ bool chol_upper(double2* G, double2* tau, int p, double* sh) {
 }
 
 // T = tau^{-1} for upper-triangular tau with real positive diagonal.
-__device__ void tri_inv_upper(const double2* tau, double2* T, int p) {
+__device__ void tri_inv_upper(const double2* tau, double2* T, int p, double* dinv) {
   for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) T[e] = cz();
+  for (int i = threadIdx.x; i < p; i += blockDim.x) dinv[i] = 1.0 / tau[i * LD + i].x;
   __syncthreads();
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    T[j * LD + j] = make_double2(1.0 / tau[j * LD + j].x, 0.0);
+    T[j * LD + j] = make_double2(dinv[j], 0.0);
     for (int i = j - 1; i >= 0; --i) {
-      double2 s = cz();
-      for (int k = i + 1; k <= j; ++k) cmac(s, tau[i * LD + k], T[k * LD + j]);
-      const double d = -1.0 / tau[i * LD + i].x;
-      T[i * LD + j] = make_double2(s.x * d, s.y * d);
+      double2 s0 = cz(), s1 = cz();
+      int k = i + 1;
+      for (; k + 2 <= j + 1; k += 2) {
+        cmac(s0, tau[i * LD + k], T[k * LD + j]);
+        cmac(s1, tau[i * LD + k + 1], T[(k + 1) * LD + j]);
+      }
+      if (k <= j) cmac(s0, tau[i * LD + k], T[k * LD + j]);
+      const double d = -dinv[i];
+      T[i * LD + j] = make_double2((s0.x + s1.x) * d, (s0.y + s1.y) * d);
     }
   }
   __syncthreads();
 }
 
 // Solve M Z = R in place (R <- Z), LU with partial pivoting; M is destroyed.
+// Pivot = largest |re| + |im| in the column (ties to the lowest row).  For non-negative
+// doubles the IEEE bit pattern orders like the value, so the warp argmax compares 64-bit
+// integers (NaN patterns sort above +inf and are then reported as a breakdown).
 __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, int* ish) {
   for (int k = 0; k < p; ++k) {
     if (threadIdx.x < 32) {
-      double best = -1.0;
+      unsigned long long best = 0ull;
       int bi = p;
       for (int i = k + threadIdx.x; i < p; i += 32) {
-        const double v = cabs1(M[i * LD + k]);
-        if (v > best || (v == best && i < bi) || v != v) {
-          best = (v != v) ? INFINITY : v;
+        const unsigned long long key = (unsigned long long)__double_as_longlong(cabs1(M[i * LD + k]));
+        if (bi == p || key > best) {
+          best = key;
           bi = i;
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
+        if (oi < p && (bi == p || ob > best || (ob == best && oi < bi))) {
           best = ob;
           bi = oi;
         }
       }
       if (threadIdx.x == 0) {
+        const double v = __longlong_as_double((long long)best);
         ish[0] = bi;
-        ish[1] = (best > 0.0 && isfinite(best)) ? 1 : 0;
+        ish[1] = (bi < p && v > 0.0 && isfinite(v)) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -210,7 +263,7 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
       }
       __syncthreads();
     }
-    const double2 pinv = crecip(M[k * LD + k]);
+    const double2 pinv = crecip_fast(M[k * LD + k]);
     for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) M[i * LD + k] = cmul(M[i * LD + k], pinv);
     __syncthreads();
     const int m = p - k - 1, w = m + nrhs;
@@ -222,9 +275,12 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
     }
     __syncthreads();
   }
+  // back substitution with the diagonal reciprocals formed once, in parallel
+  double2* dinv = reinterpret_cast<double2*>(sh);
+  for (int k = threadIdx.x; k < p; k += blockDim.x) dinv[k] = crecip(M[k * LD + k]);
+  __syncthreads();
   for (int k = p - 1; k >= 0; --k) {
-    const double2 dinv = crecip(M[k * LD + k]);
-    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) R[k * LD + c] = cmul(R[k * LD + c], dinv);
+    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) R[k * LD + c] = cmul(R[k * LD + c], dinv[k]);
     __syncthreads();
     for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
       const int i = e / nrhs, c = e % nrhs;
@@ -241,7 +297,7 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
 // ------------------------------------------------------------------------ shared layout
 struct SmallShared {
   double gs[2 * (2 * PMAX * (PMAX + 1) / 2 + 2)];
-  double red[SMALL_THREADS];
+  double red[2 * PMAX + 8];
   int ish[4];
   double2 m[6][LD * LD];
 };
@@ -276,7 +332,7 @@ __global__ void k_small_setup(int p, int method, const double* stage1, int ncomp
     if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 1; }
     return;
   }
-  tri_inv_upper(S.m[1], S.m[2], p);
+  tri_inv_upper(S.m[1], S.m[2], p, S.red);
   gstore(slot(mats, M_XI), S.m[1], p);
   gstore(slot(mats, M_TINV), S.m[2], p);
   if (method == 0) {
@@ -354,7 +410,7 @@ __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp,
     }
     return;
   }
-  tri_inv_upper(S.m[1], S.m[2], p);
+  tri_inv_upper(S.m[1], S.m[2], p, S.red);
   gload(S.m[3], slot(mats, M_XI), p);
   matmul(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
   gstore(slot(mats, M_XI), S.m[4], p);
