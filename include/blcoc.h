@@ -47,7 +47,14 @@ typedef enum {
   BLCOC_ERR_TIMEOUT = 7        /* reserved: a device wait gave up                        */
 } blcoc_status;
 
-typedef enum { BLCOC_COCG_RQ = 0, BLCOC_COCR_RQ = 1 } blcoc_method;
+/* Methods.  The _MIXED forms are iterative refinement around the rq methods: the residual
+ * R = B - A X, the p x p solves and the Cholesky QR are FP64; each correction solve
+ * A D = R runs bl_cocg_rq / bl_cocr_rq with complex64 SpMM, Grams and block updates to a
+ * relative tolerance 10^inner_tol_exp (blcoc_set_option), then X += D in FP64.  tol is
+ * then on the true residual ||B - A X||_F / ||B||_F and maxit bounds the total inner
+ * iterations; blcoc_get_info returns the inner iteration count and, as hist, the true
+ * relative residual after each refinement step. */
+typedef enum { BLCOC_COCG_RQ = 0, BLCOC_COCR_RQ = 1, BLCOC_COCG_RQ_MIXED = 2, BLCOC_COCR_RQ_MIXED = 3 } blcoc_method;
 
 /* Largest number of right-hand sides one solve accepts. */
 #define BLCOC_MAX_P 32
@@ -125,6 +132,17 @@ blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, i
  * blcoc_set_option - tuning switches (key, value):
  *   "graph"      : 1 (default) replays the iteration as a CUDA graph, 0 launches kernels.
  *   "poll"       : iterations between two host checks of the convergence flag (default 16).
+ *   "inner_tol_exp": mixed methods: inner relative tolerance 10^value, value in [-15, -1]
+ *                  (default -5).
+ *   "inner_maxit": mixed methods: iteration limit of one correction solve (0 = the
+ *                  remaining budget, default).
+ *   "outer_maxit": mixed methods: refinement steps (default 40).
+ *   "u_explicit" : BLCOC_COCR_RQ: 1 forms U_{m+1} = A S_{m+1} with a second sparse
+ *                  product per iteration instead of Algorithm 3's recurrence
+ *                  U_{m+1} = V_{m+1} + U_m beta'_m (equal in exact arithmetic; the
+ *                  recurrence is the default, 0).
+ *   "u_explicit_mixed": the same for the complex64 inner solves of BLCOC_COCR_RQ_MIXED
+ *                  (default 1: the recurrence drifts quickly in single precision).
  *   "timing"     : 1 brackets every kernel of the iterations with CUDA events on
  *                  the internal stream (also inside the graph) and accumulates per-kernel
  *                  device time; 0 (default) records nothing.
@@ -133,7 +151,8 @@ blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, i
 blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
 
 /* blcoc_get_stat - counters of the last solve: "launches" (kernels launched by the
- * solve, including those inside graph replays), "graph_replays", and with the
+ * solve, including those inside graph replays), "graph_replays", "outer_iters"
+ * (refinement steps of a mixed solve), and with the
  * "timing" option "kt_ns.<kernel>" (total device nanoseconds) and "kt_n.<kernel>"
  * (launches that did work) for <kernel> in resid, spmm_gram, spmm_plain, cocr_passA,
  * cocr_passC, cocg_pass1, cocg_pass2, reduce, small_setup, small_H0, small_alpha,

@@ -26,8 +26,11 @@ BLCOC_BREAKDOWN = 6
 BLCOC_ERR_TIMEOUT = 7
 BLCOC_COCG_RQ = 0
 BLCOC_COCR_RQ = 1
+BLCOC_COCG_RQ_MIXED = 2
+BLCOC_COCR_RQ_MIXED = 3
 BLCOC_MAX_P = 32
-METHODS = {"cocg_rq": BLCOC_COCG_RQ, "cocr_rq": BLCOC_COCR_RQ}
+METHODS = {"cocg_rq": BLCOC_COCG_RQ, "cocr_rq": BLCOC_COCR_RQ, "cocg_rq_mixed": BLCOC_COCG_RQ_MIXED,
+           "cocr_rq_mixed": BLCOC_COCR_RQ_MIXED}
 
 # name -> (restype, argtypes) for every symbol include/blcoc.h declares
 SIGNATURES = {

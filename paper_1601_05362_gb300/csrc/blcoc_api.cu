@@ -30,21 +30,26 @@ void blcoc::set_global_error(const char* msg) { g_create_error = msg; }
 
 namespace {
 
-const KernelSet* kernels_for(int p, int* PP) {
-  if (p <= 1) { *PP = 1; return &kernel_set<1>(); }
-  if (p <= 2) { *PP = 2; return &kernel_set<2>(); }
-  if (p <= 4) { *PP = 4; return &kernel_set<4>(); }
-  if (p <= 8) { *PP = 8; return &kernel_set<8>(); }
-  if (p <= 16) { *PP = 16; return &kernel_set<16>(); }
+const KernelSet* kernels_for(int p, int* PP, bool f32 = false) {
+  if (p <= 1) { *PP = 1; return f32 ? &kernel_set<1, float>() : &kernel_set<1, double>(); }
+  if (p <= 2) { *PP = 2; return f32 ? &kernel_set<2, float>() : &kernel_set<2, double>(); }
+  if (p <= 4) { *PP = 4; return f32 ? &kernel_set<4, float>() : &kernel_set<4, double>(); }
+  if (p <= 8) { *PP = 8; return f32 ? &kernel_set<8, float>() : &kernel_set<8, double>(); }
+  if (p <= 16) { *PP = 16; return f32 ? &kernel_set<16, float>() : &kernel_set<16, double>(); }
   *PP = 32;
-  return &kernel_set<32>();
+  return f32 ? &kernel_set<32, float>() : &kernel_set<32, double>();
+}
+
+__global__ void k_vals_to_c64(const double2* __restrict__ v, float2* __restrict__ o, int64_t nnz) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = make_float2((float)v[i].x, (float)v[i].y);
 }
 
 // Names of the timed kernel kinds (index = PassKind of blcoc_rowpass.cuh).
 const char* const kKindNames[] = {"resid",      "spmm_gram",  "spmm_plain", "cocr_passA", "cocr_passC",
                                   "cocg_pass1", "cocg_pass2", "reduce",     "small_setup", "small_H0",
-                                  "small_alpha", "small_chol", "small_beta", "small_trr"};
-constexpr int kNumKinds = 14;
+                                  "small_alpha", "small_chol", "small_beta", "small_trr",  "small_setup_inner"};
+constexpr int kNumKinds = 15;
 constexpr int kKindReduce = 7, kKindSmall0 = 8;   // small kernel kind = kKindSmall0 + SmallKind
 
 struct Timer {
@@ -80,6 +85,7 @@ struct blcoc_ctx {
   int* rp = nullptr;
   int* ci = nullptr;
   double2* va = nullptr;
+  float2* vaf = nullptr;      // complex64 values, made on the first mixed-precision solve
   // workspace
   int p_cap = 0;
   int64_t gen = 0;
@@ -89,6 +95,9 @@ struct blcoc_ctx {
   size_t partials_cap = 0;   // double2 entries
   double* stage1 = nullptr;
   size_t stage1_cap = 0;     // doubles
+  // complex64 workspace of the mixed-precision form (W, S, U, V, Q, D)
+  int p_cap32 = 0;
+  float2* w32[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* hist = nullptr;
   int hist_cap = 0;
   Ctrl* ctrl = nullptr;
@@ -98,6 +107,12 @@ struct blcoc_ctx {
   int use_graph = 1;
   int poll = 16;
   int timing = 0;
+  int inner_tol_exp = -5;     // mixed precision: inner tolerance 10^inner_tol_exp
+  int inner_maxit = 0;        // mixed precision: per inner solve (0 = remaining budget)
+  int outer_maxit = 40;
+  int outer_iters = 0;
+  int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
+  int u_explicit_mixed = 1;   // the same for the complex64 inner solves
   Graph graph;
   // kernel timing: event pool and per-kind totals of the last solve
   std::vector<cudaEvent_t> evpool;
@@ -139,6 +154,14 @@ blcoc_status invalid(blcoc_ctx* h, const char* msg) {
 // Partial entries per CTA for any pass: max over kinds (resid: 2 triangles + norms).
 int max_ne(int p) { return 2 * tri_count(p) + 1; }
 
+void free_ws32(blcoc_ctx* h) {
+  for (float2*& b : h->w32) {
+    if (b) cudaFree(b);
+    b = nullptr;
+  }
+  h->p_cap32 = 0;
+}
+
 void free_ws(blcoc_ctx* h) {
   double2* blocks[] = {h->W, h->S, h->U, h->V, h->Q, h->mats, h->partials};
   for (double2* b : blocks)
@@ -148,6 +171,22 @@ void free_ws(blcoc_ctx* h) {
   h->stage1 = nullptr;
   h->p_cap = 0;
   h->partials_cap = h->stage1_cap = 0;
+}
+
+blcoc_status ensure_ws32(blcoc_ctx* h, int p) {
+  if (!h->vaf) {
+    CK(h, cudaMalloc(&h->vaf, h->nnz * sizeof(float2)));
+    k_vals_to_c64<<<h->num_sms * 4, 256, 0, h->s>>>(h->va, h->vaf, h->nnz);
+    CK(h, cudaGetLastError());
+  }
+  if (p <= h->p_cap32) return BLCOC_OK;
+  h->graph.reset();
+  free_ws32(h);
+  const size_t blk = (size_t)h->n * p * sizeof(float2);
+  for (float2*& b : h->w32) CK(h, cudaMalloc(&b, blk));
+  h->p_cap32 = p;
+  h->gen++;
+  return BLCOC_OK;
 }
 
 blcoc_status ensure_ws(blcoc_ctx* h, int p) {
@@ -183,15 +222,31 @@ struct Solver {
   int PP, p, method;
   const double2* B;
   double2* X;
+  // block buffers: the FP64 workspace, or (mixed precision) the complex64 one
+  double2 *bW = nullptr, *bS = nullptr, *bU = nullptr, *bV = nullptr, *bQ = nullptr;
+  void use_fp64_blocks() {
+    bW = h->W;
+    bS = h->S;
+    bU = h->U;
+    bV = h->V;
+    bQ = h->Q;
+  }
+  void use_c64_blocks() {
+    bW = reinterpret_cast<double2*>(h->w32[0]);
+    bS = reinterpret_cast<double2*>(h->w32[1]);
+    bU = reinterpret_cast<double2*>(h->w32[2]);
+    bV = reinterpret_cast<double2*>(h->w32[3]);
+    bQ = reinterpret_cast<double2*>(h->w32[4]);
+  }
   PassArgs base() const {
     PassArgs a{};
-    a.A = CsrDev{h->n, h->nnz, h->rp, h->ci, h->va};
+    a.A = CsrDev{h->n, h->nnz, h->rp, h->ci, h->va, h->vaf};
     a.p = p;
-    a.W = h->W;
-    a.S = h->S;
-    a.U = h->U;
-    a.V = h->V;
-    a.Q = h->Q;
+    a.W = bW ? bW : h->W;
+    a.S = bS ? bS : h->S;
+    a.U = bU ? bU : h->U;
+    a.V = bV ? bV : h->V;
+    a.Q = bQ ? bQ : h->Q;
     a.X = X;
     a.B = B;
     a.mats = h->mats;
@@ -267,11 +322,13 @@ struct Solver {
   // kinds must match PassKind in blcoc_rowpass.cuh
   enum { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2 };
 
-  void setup_residual() {
+  // inner = 1: the right-hand side of this solve is the residual itself (refinement
+  // step), so the stopping test is relative to ||R||_F instead of ||B||_F.
+  void setup_residual(int inner = 0) {
     const int E = tri_count(p);
     pass(K->resid, K_RESID, 2 * E + 1, method == BLCOC_COCG_RQ ? 2 : 0);
     reduce(2 * E + 1, h->ctrl);
-    small(SK_SETUP, 2 * E + 1);
+    small(inner ? SK_SETUP_INNER : SK_SETUP, 2 * E + 1);
   }
   void setup_rest() {
     const int E = tri_count(p);
@@ -283,13 +340,38 @@ struct Solver {
       reduce(E, h->ctrl);
     } else {
       pass(K->cocg_pass2, K_COCG_2, 0, 1);     // S_0 = Q_0
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, h->S);   // A S_0, gram S^T A S
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, base().S);   // A S_0, gram S^T A S
       reduce(E, h->ctrl);
     }
   }
+  bool uexpl = false;
   void iteration() {
     const int E = tri_count(p);
-    if (method == BLCOC_COCR_RQ) {
+    if (method == BLCOC_COCR_RQ && uexpl) {
+      small(SK_ALPHA, E);
+      pass(K->cocr_passA, K_COCR_A, E, 0);
+      reduce(E, h->ctrl);
+      small(SK_CHOL, E);
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (H+ of line 8)
+      reduce(E, h->ctrl);
+      small(SK_COCR_BETA, E);
+      pass(K->cocr_passC, K_COCR_C, 0, 4);               // Q, X, S (no U recurrence)
+      {
+        PassArgs a = base();
+        a.W = a.S;                                       // gather S_{m+1}
+        a.V = a.U;                                       // U_{m+1} = A S_{m+1}
+        a.ne = E;
+        a.flag = 4;                                      // gram U^T U
+        a.grid = K->grid(h->n, K_SPMM_GRAM, h->num_sms);
+        Timer t;
+        timed_begin(t, K_SPMM_GRAM);
+        K->spmm_gram(a, h->s);
+        timed_end(t);
+        ++launches;
+        last_grid = a.grid;
+      }
+      reduce(E, h->ctrl);
+    } else if (method == BLCOC_COCR_RQ) {
       small(SK_ALPHA, E);
       pass(K->cocr_passA, K_COCR_A, E, 0);
       reduce(E, h->ctrl);
@@ -305,7 +387,7 @@ struct Solver {
       reduce(2 * E, h->ctrl);
       small(SK_CHOL, 2 * E);
       pass(K->cocg_pass2, K_COCG_2, 0, 0);
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, h->S);   // A S_{m+1}, gram S^T A S
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, base().S);   // A S_{m+1}, gram S^T A S
       reduce(E, h->ctrl);
     }
   }
@@ -362,6 +444,8 @@ blcoc_status blcoc_destroy(blcoc_handle h) {
   if (h->s) cudaStreamSynchronize(h->s);
   h->graph.reset();
   free_ws(h);
+  free_ws32(h);
+  if (h->vaf) cudaFree(h->vaf);
   if (h->Bst) cudaFree(h->Bst);
   if (h->Xst) cudaFree(h->Xst);
   if (h->rp) cudaFree(h->rp);
@@ -458,10 +542,31 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     h->timing = (int)value;
     return BLCOC_OK;
   }
+  if (!strcmp(key, "inner_tol_exp")) {
+    if (value < -15 || value > -1) return invalid(h, "inner_tol_exp must be in [-15, -1]");
+    h->inner_tol_exp = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "inner_maxit")) {
+    if (value < 0 || value > (1 << 30)) return invalid(h, "inner_maxit must be >= 0");
+    h->inner_maxit = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "outer_maxit")) {
+    if (value < 1 || value > 10000) return invalid(h, "outer_maxit must be in [1, 10000]");
+    h->outer_maxit = (int)value;
+    return BLCOC_OK;
+  }
   if (!strcmp(key, "poll")) {
     if (value < 1 || value > 4096) return invalid(h, "poll must be in [1, 4096]");
     if (h->poll != (int)value) h->graph.reset();
     h->poll = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "u_explicit") || !strcmp(key, "u_explicit_mixed")) {
+    if (value != 0 && value != 1) return invalid(h, "u_explicit must be 0 or 1");
+    h->graph.reset();
+    (key[10] == 0 ? h->u_explicit : h->u_explicit_mixed) = (int)value;
     return BLCOC_OK;
   }
   return invalid(h, "unknown option");
@@ -471,6 +576,7 @@ blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value) {
   if (!h || !key || !value) return invalid(h, "NULL argument");
   if (!strcmp(key, "launches")) { *value = h->stat_launches; return BLCOC_OK; }
   if (!strcmp(key, "graph_replays")) { *value = h->stat_replays; return BLCOC_OK; }
+  if (!strcmp(key, "outer_iters")) { *value = h->outer_iters; return BLCOC_OK; }
   for (int k = 0; k < kNumKinds; ++k) {
     const std::string nm(kKindNames[k]);
     if (("kt_ns." + nm) == key) { *value = (int64_t)(h->kt_ms[k] * 1e6); return BLCOC_OK; }
@@ -523,11 +629,203 @@ blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, i
   return BLCOC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Replays batches of `poll` iterations (captured once as a CUDA graph, or launched
+// directly) until the control block reports the end of the solve.  `gkey` identifies
+// the kernel sequence of the graph (method and working precision).
+blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
+  const int batch = h->poll;
+  const bool use_graph = h->use_graph != 0;
+  std::vector<Timer> direct_timers;
+  if (use_graph) {
+    Graph& g = h->graph;
+    if (!(g.exec && g.p == sv.p && g.method == gkey && g.batch == batch && g.X == sv.X && g.gen == h->gen &&
+          g.timing == h->timing)) {
+      g.reset();
+      h->evnext = 0;
+      cudaGraph_t graph = nullptr;
+      CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+      const int before = sv.launches;
+      sv.timers = h->timing ? &g.timers : nullptr;
+      sv.capturing = true;
+      for (int i = 0; i < batch; ++i) {
+        sv.batch_iter = i;
+        sv.iteration();
+      }
+      sv.capturing = false;
+      sv.timers = nullptr;
+      g.timing = h->timing;
+      g.launches = sv.launches - before;
+      sv.launches = before;
+      cudaError_t e = cudaStreamEndCapture(h->s, &graph);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g.exec = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+      }
+      g.p = sv.p;
+      g.method = gkey;
+      g.batch = batch;
+      g.X = sv.X;
+      g.gen = h->gen;
+    }
+  }
+  int iter_before = 0;
+  for (int done_iters = 0;; done_iters += batch) {
+    const std::vector<Timer>* timers = nullptr;
+    if (use_graph) {
+      CK(h, cudaGraphLaunch(h->graph.exec, h->s));
+      sv.launches += h->graph.launches;
+      h->stat_replays++;
+      timers = &h->graph.timers;
+    } else {
+      direct_timers.clear();
+      if (h->timing) {
+        h->evnext = 0;
+        sv.timers = &direct_timers;
+      }
+      for (int i = 0; i < batch; ++i) {
+        sv.batch_iter = i;
+        sv.iteration();
+      }
+      sv.timers = nullptr;
+      CK(h, cudaGetLastError());
+      timers = &direct_timers;
+    }
+    CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    if (h->timing && timers) {
+      // kernels of iterations past the end returned at once: not counted
+      const int ran = h->h_ctrl->iter - iter_before;
+      for (const Timer& t : *timers) {
+        if (t.iter >= ran) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+          h->kt_ms[t.kind] += ms;
+          h->kt_n[t.kind] += 1;
+        } else {
+          cudaGetLastError();   // timing is best effort; never fail the solve for it
+        }
+      }
+    }
+    iter_before = h->h_ctrl->iter;
+    if (h->h_ctrl->done) break;
+    if (done_iters > maxit + 2 * batch) {
+      h->err = "iteration control did not stop";
+      return BLCOC_ERR_CUDA;
+    }
+  }
+  return BLCOC_OK;
+}
+
+blcoc_status finish_solve(blcoc_ctx* h, Solver& sv, void* X, bool hostX, size_t bytes) {
+  if (hostX) CK(h, cudaMemcpyAsync(X, h->Xst, bytes, cudaMemcpyDeviceToHost, h->s));
+  CK(h, cudaEventRecord(h->ev, h->s));
+  CK(h, cudaStreamWaitEvent(h->user_stream, h->ev, 0));
+  CK(h, cudaStreamSynchronize(h->s));
+  h->stat_launches = sv.launches;
+  return BLCOC_OK;
+}
+
+// Mixed precision (SURVEY form f2): iterative refinement whose residual R = B - A X, the
+// p x p solves and the Cholesky QR are FP64, and whose inner correction solve A D = R
+// (bl_cocr_rq or bl_cocg_rq) runs its SpMM, Grams and block updates in complex64.
+blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, bool hostX, int p, int inner_method,
+                         double tol, int maxit) {
+  blcoc_status st = ensure_ws32(h, p);
+  if (st != BLCOC_OK) return st;
+  const size_t bytes = (size_t)h->n * p * sizeof(double2);
+  int PP = 0;
+  Solver sv{h, kernels_for(p, &PP, true), PP, p, inner_method, dB, dX};
+  sv.K->prepare();
+  sv.use_c64_blocks();
+  sv.uexpl = h->u_explicit_mixed != 0;
+  double2* D = reinterpret_cast<double2*>(h->w32[5]);
+  const int gkey = 100 + inner_method + (sv.uexpl ? 10 : 0);
+  std::vector<double> outer_hist;
+  int total_inner = 0, outer = 0, done = 2, last_bd = 0;
+  double bnorm = 0.0, relres = 0.0;
+  for (;; ++outer) {
+    // FP64 residual of the current X, stored in complex64 as the inner right-hand side
+    Ctrl c0{};
+    const int left = maxit - total_inner;
+    c0.maxit = h->inner_maxit > 0 && h->inner_maxit < left ? h->inner_maxit : left;
+    c0.tol = std::pow(10.0, (double)h->inner_tol_exp);
+    CK(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->s));
+    sv.X = dX;
+    sv.setup_residual(1);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    const Ctrl c = *h->h_ctrl;
+    if (outer == 0) bnorm = std::sqrt(c.pad[0]);
+    if (bnorm == 0.0) {   // B = 0: X = 0 solves it exactly
+      CK(h, cudaMemsetAsync(dX, 0, bytes, h->s));
+      outer_hist.push_back(0.0);
+      done = 1;
+      relres = 0.0;
+      break;
+    }
+    relres = c.trr / bnorm;
+    outer_hist.push_back(relres);
+    if (!std::isfinite(relres)) { done = 3; last_bd = 5; break; }
+    if (relres <= tol) { done = 1; break; }
+    if (total_inner >= maxit || outer >= h->outer_maxit) { done = 2; break; }
+    if (c.done == 3) { done = 3; last_bd = c.bd_code; break; }   // residual block without full rank
+    CK(h, cudaMemsetAsync(D, 0, (size_t)h->n * p * sizeof(float2), h->s));
+    sv.X = D;
+    sv.setup_rest();
+    CK(h, cudaGetLastError());
+    st = run_iterations(h, sv, gkey, c0.maxit);
+    if (st != BLCOC_OK) return st;
+    const Ctrl ci = *h->h_ctrl;
+    total_inner += ci.iter;
+    if (ci.done == 3 && ci.iter == 0) { done = 3; last_bd = ci.bd_code; break; }
+    // X += D in FP64
+    PassArgs a = sv.base();
+    a.X = dX;
+    a.V = D;
+    a.grid = sv.K->grid(h->n, 7, h->num_sms);
+    sv.K->axpy(a, h->s);
+    ++sv.launches;
+    CK(h, cudaGetLastError());
+  }
+  h->outer_iters = outer;
+  h->iters = total_inner;
+  h->trr = relres;
+  h->relres = relres;
+  h->hist_h = outer_hist;
+  h->xi_h.assign(2 * p * p, 0.0);
+  st = finish_solve(h, sv, X, hostX, bytes);
+  if (st != BLCOC_OK) return st;
+  switch (done) {
+    case 1: return BLCOC_OK;
+    case 2: return BLCOC_NOT_CONVERGED;
+    default: {
+      char buf[128];
+      snprintf(buf, sizeof buf, "breakdown in refinement step %d (site %d)", outer, last_bd);
+      h->err = buf;
+      return BLCOC_BREAKDOWN;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_method method, double tol, int maxit) {
   if (!h) return invalid(h, "NULL handle");
   h->err.clear();
   if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
-  if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ) return invalid(h, "unknown method");
+  if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ && method != BLCOC_COCG_RQ_MIXED &&
+      method != BLCOC_COCR_RQ_MIXED)
+    return invalid(h, "unknown method");
   if (!(tol >= 0.0) || std::isinf(tol)) return invalid(h, "tol must be finite and >= 0");
   if (maxit < 0) return invalid(h, "maxit must be >= 0");
   if (!B || !X || B == X) return invalid(h, "B and X must be distinct non-NULL pointers");
@@ -563,9 +861,21 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
     CK(h, cudaMemcpyAsync(h->Xst, X, bytes, cudaMemcpyHostToDevice, h->s));
     dX = h->Xst;
   }
+  h->stat_replays = 0;
+  h->outer_iters = 0;
+  for (int k = 0; k < kNumKinds; ++k) {
+    h->kt_ms[k] = 0.0;
+    h->kt_n[k] = 0;
+  }
+  if (method == BLCOC_COCG_RQ_MIXED || method == BLCOC_COCR_RQ_MIXED)
+    return solve_mixed(h, dB, dX, X, hostX, p, method == BLCOC_COCR_RQ_MIXED ? BLCOC_COCR_RQ : BLCOC_COCG_RQ, tol,
+                       maxit);
+
   int PP = 0;
   Solver sv{h, kernels_for(p, &PP), PP, p, (int)method, dB, dX};
   sv.K->prepare();
+  sv.use_fp64_blocks();
+  sv.uexpl = h->u_explicit != 0;
   Ctrl c0{};
   c0.maxit = maxit;
   c0.tol = tol;
@@ -574,11 +884,6 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   CK(h, cudaGetLastError());
   CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
   CK(h, cudaStreamSynchronize(h->s));
-  h->stat_replays = 0;
-  for (int k = 0; k < kNumKinds; ++k) {
-    h->kt_ms[k] = 0.0;
-    h->kt_n[k] = 0;
-  }
   bool zero_rhs = false;
   if (h->h_ctrl->done == 1 && h->h_ctrl->sumsq_b == 0.0) {
     zero_rhs = true;
@@ -586,89 +891,8 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   } else if (!h->h_ctrl->done) {
     sv.setup_rest();
     CK(h, cudaGetLastError());
-    const int batch = h->poll;
-    bool use_graph = h->use_graph != 0;
-    std::vector<Timer> direct_timers;
-    if (use_graph) {
-      Graph& g = h->graph;
-      if (!(g.exec && g.p == p && g.method == (int)method && g.batch == batch && g.X == dX && g.gen == h->gen &&
-            g.timing == h->timing)) {
-        g.reset();
-        h->evnext = 0;
-        cudaGraph_t graph = nullptr;
-        CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-        const int before = sv.launches;
-        sv.timers = h->timing ? &g.timers : nullptr;
-        sv.capturing = true;
-        for (int i = 0; i < batch; ++i) {
-          sv.batch_iter = i;
-          sv.iteration();
-        }
-        sv.capturing = false;
-        sv.timers = nullptr;
-        g.timing = h->timing;
-        g.launches = sv.launches - before;
-        sv.launches = before;
-        cudaError_t e = cudaStreamEndCapture(h->s, &graph);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&g.exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-          g.exec = nullptr;
-          return cuda_fail(h, e, "cudaGraphInstantiate");
-        }
-        g.p = p;
-        g.method = (int)method;
-        g.batch = batch;
-        g.X = dX;
-        g.gen = h->gen;
-      }
-    }
-    int iter_before = 0;
-    for (int done_iters = 0;; done_iters += batch) {
-      const std::vector<Timer>* timers = nullptr;
-      if (use_graph) {
-        CK(h, cudaGraphLaunch(h->graph.exec, h->s));
-        sv.launches += h->graph.launches;
-        h->stat_replays++;
-        timers = &h->graph.timers;
-      } else {
-        direct_timers.clear();
-        if (h->timing) {
-          h->evnext = 0;
-          sv.timers = &direct_timers;
-        }
-        for (int i = 0; i < batch; ++i) {
-          sv.batch_iter = i;
-          sv.iteration();
-        }
-        sv.timers = nullptr;
-        CK(h, cudaGetLastError());
-        timers = &direct_timers;
-      }
-      CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
-      CK(h, cudaStreamSynchronize(h->s));
-      if (h->timing && timers) {
-        // kernels of iterations past the end returned at once: not counted
-        const int ran = h->h_ctrl->iter - iter_before;
-        for (const Timer& t : *timers) {
-          if (t.iter >= ran) continue;
-          float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
-            h->kt_ms[t.kind] += ms;
-            h->kt_n[t.kind] += 1;
-          } else {
-            cudaGetLastError();   // timing is best effort; never fail the solve for it
-          }
-        }
-      }
-      iter_before = h->h_ctrl->iter;
-      if (h->h_ctrl->done) break;
-      if (done_iters > maxit + 2 * batch) {
-        h->err = "iteration control did not stop";
-        return BLCOC_ERR_CUDA;
-      }
-    }
+    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0), maxit);
+    if (st != BLCOC_OK) return st;
   }
   // true residual of the returned iterate
   sv.B = dB;
@@ -690,11 +914,8 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   h->xi_h.assign(2 * p * p, 0.0);
   CK(h, cudaMemcpy(h->xi_h.data(), h->mats + M_XI * PMAX * PMAX, (size_t)p * p * sizeof(double2),
                    cudaMemcpyDeviceToHost));
-  if (hostX) CK(h, cudaMemcpyAsync(X, h->Xst, bytes, cudaMemcpyDeviceToHost, h->s));
-  CK(h, cudaEventRecord(h->ev, h->s));
-  CK(h, cudaStreamWaitEvent(h->user_stream, h->ev, 0));
-  CK(h, cudaStreamSynchronize(h->s));
-  h->stat_launches = sv.launches;
+  st = finish_solve(h, sv, X, hostX, bytes);
+  if (st != BLCOC_OK) return st;
   if (zero_rhs) return BLCOC_OK;
   switch (c.done) {
     case 1: return BLCOC_OK;

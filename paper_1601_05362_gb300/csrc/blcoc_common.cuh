@@ -51,6 +51,18 @@ __host__ __device__ inline int tri_count(int p) { return p * (p + 1) / 2; }
 // ----------------------------------------------------------------------------- complex
 __device__ __forceinline__ double2 cz() { return make_double2(0.0, 0.0); }
 
+// complex element type of a working precision: double -> double2, float -> float2
+template <typename S> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+template <typename C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+// conversions between the working precision and the FP64 factors / FP64 results
+template <typename C> __device__ __forceinline__ C from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
 // acc += a * b  (4 DFMA)
 __device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
   acc.x = fma(a.x, b.x, acc.x);
@@ -73,6 +85,26 @@ __device__ __forceinline__ void cmac_conj(double2& acc, double2 a, double2 b) {
   acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// single-precision counterparts (complex64 working precision)
+__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmsub(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(-a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(-a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
 // ----------------------------------------------------------------------------- launch table
 struct CsrDev {
   int64_t n;
@@ -80,6 +112,7 @@ struct CsrDev {
   const int* rp;
   const int* ci;
   const double2* va;
+  const float2* vaf;   // complex64 copy of the values (mixed-precision inner solves)
 };
 
 struct PassArgs {
@@ -111,11 +144,15 @@ struct KernelSet {
   LaunchFn cocr_passC;   // Q = W T (stored); X += S alpha'xi; S = Q + S beta'; U = V + U beta'; gram U^T U
   LaunchFn cocg_pass1;   // W <- Q - (AS) alpha'; X += S alpha'xi; grams W^H W, W^T W
   LaunchFn cocg_pass2;   // Q = W T (stored); S <- Q + S beta'
+  LaunchFn axpy;         // X (FP64) += D (working precision), the refinement update
   int (*grid)(int64_t n, int kind, int num_sms);
   void (*prepare)();     // set the dynamic shared-memory limits (once per device)
 };
 
-template <int PP> const KernelSet& kernel_set();
+// S = double: the FP64 path; S = float: complex64 working precision for the inner solves
+// of the mixed-precision refinement (the residual pass stays FP64 and writes its R in
+// complex64, the Grams are summed in FP64, the p x p stages are the FP64 kernels).
+template <int PP, typename S = double> const KernelSet& kernel_set();
 
 // Sets the message blcoc_last_error(NULL) returns (calling thread only).
 void set_global_error(const char* msg);

@@ -1,5 +1,6 @@
 // Row-pass kernels of bl_cocg_rq / bl_cocr_rq (Algorithms 2-3, Sec. 2.2), templated on
-// the block width PP (the solve's p satisfies p <= PP).
+// the block width PP (the solve's p satisfies p <= PP) and on the working precision S
+// (double: the FP64 path; float: the complex64 inner solves of the mixed-precision form).
 //
 // Work decomposition.  On GB300 every FP64 operation of this path is issued by the FP64
 // pipe (about 2 DFMA per clock per SM), which binds long before HBM does; the design
@@ -10,7 +11,8 @@
 //     (k, j) sequence, so the upper-triangular tau^{-1} applies cost exactly p(p+1)/2
 //     complex MACs per row and the p x p factor is a shared-memory broadcast;
 //   * Gram products G = Y^T Z (or Y^H Z) over the chunk run with lane = Gram entry;
-//     symmetric / Hermitian Grams compute only the upper triangle;
+//     symmetric / Hermitian Grams compute only the upper triangle, and the remainder
+//     entries are spread over row groups so every lane does the same work;
 //   * per-CTA Gram partials are summed in a fixed order (first here, then by a
 //     deterministic two-stage reduction), so results are bitwise reproducible.
 // Tiles are [k][32 rows] with the row index XOR-swizzled by (k & 7): lane = row reads,
@@ -22,63 +24,85 @@
 
 namespace blcoc {
 
-template <int PP>
+template <int PP, typename S = double>
 struct Geo {
-  static constexpr int TILE = PP * CHUNK;                      // double2 per staged block
-  static constexpr int NFULL = (PP * PP + 31) / 32;            // gram slots per lane, full
+  using C = typename Cx<S>::T;
+  static constexpr int TILE = PP * CHUNK;                      // elements per staged block
   static constexpr int NTRI = (PP * (PP + 1) / 2 + 31) / 32;   // gram slots per lane, triangle
   static constexpr int JB = PP >= 8 ? 8 : PP;                  // output columns per apply sweep
-  static constexpr bool MATS_SMEM = PP <= 16;                  // p x p factors staged in smem
+  static constexpr bool MATS_SMEM = PP <= 16 || sizeof(S) == 4;  // p x p factors staged in smem
   static constexpr int LPR = PP < 32 ? PP : 32;                // lanes per row in the CSR gather
   static constexpr int RPI = 32 / LPR;                         // rows per gather instruction
 };
 
 __device__ __forceinline__ int tix(int k, int r) { return k * CHUNK + (r ^ (k & 7)); }
 
+// Elements taken by nm staged p x p factors, rounded up to a 16-byte boundary so that the
+// tiles (and the FP64 reduction area that reuses them) stay 16-byte aligned.
+template <int PP, typename S>
+constexpr int mats_off(int nm) {
+  using C = typename Cx<S>::T;
+  return Geo<PP, S>::MATS_SMEM ? (int)((((size_t)nm * PP * PP * sizeof(C) + 15) / 16 * 16) / sizeof(C)) : 0;
+}
+
 // ---------------------------------------------------------------------------------- tiles
 // Coalesced load of rows [r0, r0+32) (clipped to n) of a row-major n x p block into a
 // swizzled tile; rows past n are zero.
-template <int PP>
-__device__ __forceinline__ void load_tile(double2* t, const double2* __restrict__ g, int64_t r0, int64_t n, int p,
-                                          int lane) {
+template <int PP, typename C>
+__device__ __forceinline__ void load_tile(C* t, const C* __restrict__ g, int64_t r0, int64_t n, int p, int lane) {
   const int rows = (int)min((int64_t)CHUNK, n - r0);
   const int total = CHUNK * p;
   const int valid = rows * p;
-  const double2* src = g + r0 * p;
+  const C* src = g + r0 * p;
   for (int e = lane; e < total; e += 32) {
     const int r = e / p, k = e - r * p;
-    t[tix(k, r)] = (e < valid) ? src[e] : cz();
+    t[tix(k, r)] = (e < valid) ? src[e] : czero<C>();
   }
 }
 
-template <int PP>
-__device__ __forceinline__ void store_tile(double2* __restrict__ g, const double2* t, int64_t r0, int64_t n, int p,
-                                           int lane) {
+template <int PP, typename C>
+__device__ __forceinline__ void store_tile(C* __restrict__ g, const C* t, int64_t r0, int64_t n, int p, int lane) {
   const int rows = (int)min((int64_t)CHUNK, n - r0);
   const int valid = rows * p;
-  double2* dst = g + r0 * p;
+  C* dst = g + r0 * p;
   for (int e = lane; e < valid; e += 32) {
     const int r = e / p, k = e - r * p;
     dst[e] = t[tix(k, r)];
   }
 }
 
-// Stage a p x p factor (row stride p in global) as PP x PP, zero padded.
+// FP64 tile -> complex64 block (the residual pass of the mixed-precision form)
 template <int PP>
-__device__ __forceinline__ void load_mat(double2* s, const double2* __restrict__ g, int p) {
-  for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
-    const int k = e / PP, j = e - k * PP;
-    s[e] = (k < p && j < p) ? g[k * p + j] : cz();
+__device__ __forceinline__ void store_tile_f32(float2* __restrict__ g, const double2* t, int64_t r0, int64_t n, int p,
+                                               int lane) {
+  const int rows = (int)min((int64_t)CHUNK, n - r0);
+  const int valid = rows * p;
+  float2* dst = g + r0 * p;
+  for (int e = lane; e < valid; e += 32) {
+    const int r = e / p, k = e - r * p;
+    dst[e] = from_d2<float2>(t[tix(k, r)]);
   }
 }
 
-// Factor access: shared memory (stride PP) or global memory through the read-only path.
-template <int PP>
+// Stage a p x p FP64 factor (row stride p in global) as PP x PP in the working precision,
+// zero padded.
+template <int PP, typename C>
+__device__ __forceinline__ void load_mat(C* s, const double2* __restrict__ g, int p) {
+  for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
+    const int k = e / PP, j = e - k * PP;
+    s[e] = (k < p && j < p) ? from_d2<C>(g[k * p + j]) : czero<C>();
+  }
+}
+
+// Factor access: shared memory (stride PP) or, for FP64 at PP = 32, global memory
+// through the read-only path (row stride p).
+template <int PP, typename S>
 struct Fac {
-  const double2* m;
+  using C = typename Cx<S>::T;
+  const C* m;
   int ld;
-  __device__ __forceinline__ double2 operator()(int k, int j) const {
-    if constexpr (Geo<PP>::MATS_SMEM) return m[k * PP + j];
+  __device__ __forceinline__ C operator()(int k, int j) const {
+    if constexpr (Geo<PP, S>::MATS_SMEM) return m[k * PP + j];
     else return __ldg(m + k * ld + j);
   }
 };
@@ -87,22 +111,23 @@ struct Fac {
 // t <- t * T with T upper triangular (lane = row).  Columns are produced from the last
 // block to the first, so a column slot is overwritten only after every later column
 // that needs it has been formed.  Cost: exactly sum_j (j+1) complex MACs per row.
-template <int PP>
-__device__ __forceinline__ void tri_apply_inplace(double2* t, const Fac<PP>& T, int p, int lane) {
-  constexpr int JB = Geo<PP>::JB;
+template <int PP, typename S>
+__device__ __forceinline__ void tri_apply_inplace(typename Cx<S>::T* t, const Fac<PP, S>& T, int p, int lane) {
+  using C = typename Cx<S>::T;
+  constexpr int JB = Geo<PP, S>::JB;
   for (int j0 = ((p - 1) / JB) * JB; j0 >= 0; j0 -= JB) {
-    double2 acc[JB];
+    C acc[JB];
 #pragma unroll
-    for (int jj = 0; jj < JB; ++jj) acc[jj] = cz();
+    for (int jj = 0; jj < JB; ++jj) acc[jj] = czero<C>();
     for (int k = 0; k < j0; ++k) {
-      const double2 y = t[tix(k, lane)];
+      const C y = t[tix(k, lane)];
 #pragma unroll
       for (int jj = 0; jj < JB; ++jj) cmac(acc[jj], y, T(k, j0 + jj));
     }
 #pragma unroll
     for (int kk = 0; kk < JB; ++kk) {
       if (j0 + kk < p) {
-        const double2 y = t[tix(j0 + kk, lane)];
+        const C y = t[tix(j0 + kk, lane)];
 #pragma unroll
         for (int jj = kk; jj < JB; ++jj) cmac(acc[jj], y, T(j0 + kk, j0 + jj));
       }
@@ -115,16 +140,17 @@ __device__ __forceinline__ void tri_apply_inplace(double2* t, const Fac<PP>& T, 
 
 // out <- base + in * M  (SUB: base - in * M), lane = row.  `out` may be `base`
 // (each column of base is read only for the same column of out) but not `in`.
-template <int PP, bool SUB>
-__device__ __forceinline__ void apply_full(double2* out, const double2* base, const double2* in, const Fac<PP>& M,
-                                           int p, int lane) {
-  constexpr int JB = Geo<PP>::JB;
+template <int PP, typename S, bool SUB>
+__device__ __forceinline__ void apply_full(typename Cx<S>::T* out, const typename Cx<S>::T* base,
+                                           const typename Cx<S>::T* in, const Fac<PP, S>& M, int p, int lane) {
+  using C = typename Cx<S>::T;
+  constexpr int JB = Geo<PP, S>::JB;
   for (int j0 = 0; j0 < p; j0 += JB) {
-    double2 acc[JB];
+    C acc[JB];
 #pragma unroll
-    for (int jj = 0; jj < JB; ++jj) acc[jj] = (j0 + jj < p) ? base[tix(j0 + jj, lane)] : cz();
+    for (int jj = 0; jj < JB; ++jj) acc[jj] = (j0 + jj < p) ? base[tix(j0 + jj, lane)] : czero<C>();
     for (int k = 0; k < p; ++k) {
-      const double2 y = in[tix(k, lane)];
+      const C y = in[tix(k, lane)];
 #pragma unroll
       for (int jj = 0; jj < JB; ++jj) {
         if constexpr (SUB) cmsub(acc[jj], y, M(k, j0 + jj));
@@ -140,12 +166,15 @@ __device__ __forceinline__ void apply_full(double2* out, const double2* base, co
 // ---------------------------------------------------------------------------------- grams
 enum GramKind { G_FULL = 0, G_SYM = 1, G_HERM = 2 };
 
-template <int NS>
+template <int NS, typename S>
 struct GramAcc {
   // Entries e = lane + 32 i (i < F) take all 32 rows of a chunk.  The Er = E mod 32
   // remainder entries, when Er divides 32, are spread over G = 32/Er row groups so that
   // every lane does the same number of MACs (a warp instruction costs the same with
   // idle lanes); the G partial sums are combined by shuffles at the end.
+  // FP64: products accumulate directly in FP64.  complex64: each chunk's products
+  // accumulate in FP32 and the chunk total is added to the FP64 accumulator.
+  using C = typename Cx<S>::T;
   double2 acc[NS];
   short a[NS], b[NS];
   int E, F, Er, G;
@@ -179,21 +208,20 @@ struct GramAcc {
     if (i == F && G > 1) return 32 * F + lane % Er;
     return lane + 32 * i;
   }
-  template <bool CONJ>
-  __device__ __forceinline__ void mac(int i, const double2* Y, const double2* Z, int r) {
-    const double2 y = Y[tix(a[i], r)];
-    const double2 z = Z[tix(b[i], r)];
-    if constexpr (CONJ) cmac_conj(acc[i], y, z);
-    else cmac(acc[i], y, z);
+  template <bool CONJ, typename A>
+  __device__ __forceinline__ void mac(A& dst, int i, const C* Y, const C* Z, int r) const {
+    const C y = Y[tix(a[i], r)];
+    const C z = Z[tix(b[i], r)];
+    if constexpr (CONJ) cmac_conj(dst, y, z);
+    else cmac(dst, y, z);
   }
-  // acc[e] += sum_r op(Y[r][a_e]) Z[r][b_e] over the 32 rows of a chunk
-  template <bool CONJ>
-  __device__ __forceinline__ void add(const double2* Y, const double2* Z, int lane) {
+  template <bool CONJ, typename A>
+  __device__ __forceinline__ void add_rows(A* dst, const C* Y, const C* Z, int lane) const {
 #pragma unroll 2
     for (int r = 0; r < CHUNK; ++r) {
 #pragma unroll
       for (int i = 0; i < NS; ++i)
-        if (i < F) mac<CONJ>(i, Y, Z, r);
+        if (i < F) mac<CONJ>(dst[i], i, Y, Z, r);
     }
     if (F < NS && Er > 0) {
       if (G > 1) {
@@ -201,14 +229,31 @@ struct GramAcc {
         for (int r = r0; r < r0 + rows; ++r) {
 #pragma unroll
           for (int i = 0; i < NS; ++i)
-            if (i == F) mac<CONJ>(i, Y, Z, r);
+            if (i == F) mac<CONJ>(dst[i], i, Y, Z, r);
         }
       } else if (lane < Er) {
         for (int r = 0; r < CHUNK; ++r) {
 #pragma unroll
           for (int i = 0; i < NS; ++i)
-            if (i == F) mac<CONJ>(i, Y, Z, r);
+            if (i == F) mac<CONJ>(dst[i], i, Y, Z, r);
         }
+      }
+    }
+  }
+  // acc[e] += sum_r op(Y[r][a_e]) Z[r][b_e] over the 32 rows of a chunk
+  template <bool CONJ>
+  __device__ __forceinline__ void add(const C* Y, const C* Z, int lane) {
+    if constexpr (sizeof(S) == 8) {
+      add_rows<CONJ>(acc, Y, Z, lane);
+    } else {
+      C part[NS];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) part[i] = czero<C>();
+      add_rows<CONJ>(part, Y, Z, lane);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        acc[i].x += (double)part[i].x;
+        acc[i].y += (double)part[i].y;
       }
     }
   }
@@ -230,9 +275,9 @@ struct GramAcc {
 
 // Sum the warps' accumulators of one Gram in a fixed order and write the CTA partial.
 // `red` is shared scratch of at least NWARP*E double2; caller syncs before reuse.
-template <int NS>
-__device__ __forceinline__ void cta_write_gram(GramAcc<NS>& g, double2* red, double2* __restrict__ out,
-                                               int warp, int lane) {
+template <int NS, typename S>
+__device__ __forceinline__ void cta_write_gram(GramAcc<NS, S>& g, double2* red, double2* __restrict__ out, int warp,
+                                               int lane) {
   g.fold();
 #pragma unroll
   for (int i = 0; i < NS; ++i) {
@@ -255,33 +300,33 @@ __device__ __forceinline__ void cta_write_gram(GramAcc<NS>& g, double2* red, dou
 // ---------------------------------------------------------------------------------- gather
 // Y[r][k] = sum_j a_{row,j} X[j][k] (lanes = columns, PP/32 rows per instruction), written
 // to a swizzled tile.  RESID: Y = B - A X, also accumulating |B|^2 and |Y|^2 per lane.
-template <int PP, bool RESID>
-__device__ __forceinline__ void gather_rows(double2* Yt, const CsrDev& A, const double2* __restrict__ Xg,
-                                            const double2* __restrict__ Bg, int64_t r0, int p, int lane,
-                                            double& sb, double& sr) {
+template <int PP, typename C, bool RESID>
+__device__ __forceinline__ void gather_rows(C* Yt, const CsrDev& A, const C* __restrict__ va, const C* __restrict__ Xg,
+                                            const C* __restrict__ Bg, int64_t r0, int p, int lane, double& sb,
+                                            double& sr) {
   constexpr int LPR = Geo<PP>::LPR, RPI = Geo<PP>::RPI;
   const int sub = lane / LPR, k = lane - sub * LPR;
   for (int rr = 0; rr < CHUNK; rr += RPI) {
     const int r = rr + sub;
     const int64_t row = r0 + r;
-    double2 acc = cz();
+    C acc = czero<C>();
     if (row < A.n && k < p) {
       if constexpr (RESID) {
         acc = Bg[row * p + k];
-        sb = fma(acc.x, acc.x, sb);
-        sb = fma(acc.y, acc.y, sb);
+        sb = fma((double)acc.x, (double)acc.x, sb);
+        sb = fma((double)acc.y, (double)acc.y, sb);
       }
       const int beg = A.rp[row], end = A.rp[row + 1];
       for (int j = beg; j < end; ++j) {
         const int c = __ldg(A.ci + j);
-        const double2 a = __ldg(A.va + j);
-        const double2 x = Xg[(int64_t)c * p + k];
-        if constexpr (RESID) cmsub(acc, a, x);
-        else cmac(acc, a, x);
+        const C av = __ldg(va + j);
+        const C x = Xg[(int64_t)c * p + k];
+        if constexpr (RESID) cmsub(acc, av, x);
+        else cmac(acc, av, x);
       }
       if constexpr (RESID) {
-        sr = fma(acc.x, acc.x, sr);
-        sr = fma(acc.y, acc.y, sr);
+        sr = fma((double)acc.x, (double)acc.x, sr);
+        sr = fma((double)acc.y, (double)acc.y, sr);
       }
     }
     Yt[tix(k, r)] = acc;
@@ -298,37 +343,50 @@ __device__ __forceinline__ double warp_sum_fixed(double v) {
 // PassArgs::flag bits
 constexpr int F_FIRST = 1;      // setup variant of a pass / norm-only residual / apply T
 constexpr int F_SYM2 = 2;       // residual pass: also R^T R
+constexpr int F_UEXPL = 4;      // explicit-U variant: SpMM gram Y^T Y; pass C without the U update
 constexpr int F_FORCE = 16;     // run even when the control block says the solve is done
-#define BLCOC_PROLOGUE                                  \
-  if (!(a.flag & F_FORCE) && a.ctrl->done) return;      \
-  extern __shared__ __align__(16) double2 smem[];       \
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31; \
-  const int64_t n = a.A.n;                              \
-  const int p = a.p;                                    \
-  const int64_t nchunks = (n + CHUNK - 1) / CHUNK;      \
+
+#define BLCOC_PROLOGUE(CT)                                          \
+  if (!(a.flag & F_FORCE) && a.ctrl->done) return;                  \
+  extern __shared__ __align__(16) unsigned char smem_raw[];         \
+  CT* smem = reinterpret_cast<CT*>(smem_raw);                       \
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;       \
+  const int64_t n = a.A.n;                                          \
+  const int p = a.p;                                                \
+  const int64_t nchunks = (n + CHUNK - 1) / CHUNK;                  \
   const int64_t cstride = (int64_t)gridDim.x * NWARP;
 
-// R = B - A X (Sec. 3 residual, setup line 1 of Algorithms 2-3).
-// flag&1: norms only; flag&2: also R^T R (cocg).  Partials: [R^H R tri][R^T R tri][sum|B|^2, sum|R|^2]
-template <int PP>
+template <typename C>
+__device__ __forceinline__ C* blk(double2* p) { return reinterpret_cast<C*>(p); }
+template <typename S>
+__device__ __forceinline__ const typename Cx<S>::T* vals_of(const CsrDev& A) {
+  if constexpr (sizeof(S) == 8) return A.va;
+  else return A.vaf;
+}
+
+// R = B - A X in FP64 (Sec. 3 residual, setup line 1 of Algorithms 2-3); R is written in
+// the working precision S.  flag&1: norms only; flag&2: also R^T R (cocg).
+// Partials: [R^H R tri][R^T R tri][sum|B|^2, sum|R|^2]
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
-  BLCOC_PROLOGUE
+  BLCOC_PROLOGUE(double2)
   using G = Geo<PP>;
-  const bool norm_only = a.flag & 1, sym2 = a.flag & 2;
+  const bool norm_only = a.flag & F_FIRST, sym2 = a.flag & F_SYM2;
   double2* tR = smem + warp * G::TILE;
   double2* red = smem;
-  GramAcc<G::NTRI> gh, gs;
+  GramAcc<G::NTRI, double> gh, gs;
   gh.init(G_HERM, p, lane);
   gs.init(G_SYM, p, lane);
   double sb = 0.0, sr = 0.0;
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    gather_rows<PP, true>(tR, a.A, a.X, a.B, r0, p, lane, sb, sr);
+    gather_rows<PP, double2, true>(tR, a.A, a.A.va, a.X, a.B, r0, p, lane, sb, sr);
     if (!norm_only) {
       __syncwarp();
       gh.template add<true>(tR, tR, lane);
       if (sym2) gs.template add<false>(tR, tR, lane);
-      store_tile<PP>(a.W, tR, r0, n, p, lane);
+      if constexpr (sizeof(S) == 8) store_tile<PP>(a.W, tR, r0, n, p, lane);
+      else store_tile_f32<PP>(blk<float2>(a.W), tR, r0, n, p, lane);
     }
     __syncwarp();
   }
@@ -352,256 +410,292 @@ __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
 
 // Y = A W over the chunk, W = the block in a.W; gram W^T Y (symmetric since A = A^T);
 // out = Y T (flag=1, cocr: V = A Q = (A W) tau^{-1}) or out = Y (flag=0, cocg: a.W = S,
-// out = A S).  Partials: [W^T Y tri].
-template <int PP>
+// out = A S).  flag&F_UEXPL: gram Y^T Y instead (explicit U = A S and U^T U).
+// Partials: [W^T Y or Y^T Y tri].
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
-  BLCOC_PROLOGUE
-  using G = Geo<PP>;
-  double2* T_s = smem;
-  double2* tiles = smem + (G::MATS_SMEM ? PP * PP : 0);
-  double2* tY = tiles + warp * 2 * G::TILE;
-  double2* tW = tY + G::TILE;
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
+  C* T_s = smem;
+  C* tiles = smem + mats_off<PP, S>(1);
+  C* tY = tiles + warp * 2 * G::TILE;
+  C* tW = tY + G::TILE;
   const bool applyT = a.flag & 1;
   if constexpr (G::MATS_SMEM) {
     load_mat<PP>(T_s, a.mats + M_TINV * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> T{G::MATS_SMEM ? T_s : a.mats + M_TINV * PMAX * PMAX, p};
-  GramAcc<G::NTRI> g;
+  Fac<PP, S> T{G::MATS_SMEM ? T_s : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
+  GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
   double dummy0 = 0.0, dummy1 = 0.0;
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    gather_rows<PP, false>(tY, a.A, a.W, nullptr, r0, p, lane, dummy0, dummy1);
-    load_tile<PP>(tW, a.W, r0, n, p, lane);
+    gather_rows<PP, C, false>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
+    load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
-    g.template add<false>(tW, tY, lane);
+    g.template add<false>((a.flag & F_UEXPL) ? tY : tW, tY, lane);
     if (applyT) {
-      tri_apply_inplace<PP>(tY, T, p, lane);
+      tri_apply_inplace<PP, S>(tY, T, p, lane);
       __syncwarp();
     }
-    store_tile<PP>(a.V, tY, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.V), tY, r0, n, p, lane);
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
 }
 
 // Y = A W, nothing else (blcoc_spmm).
-template <int PP>
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
-  BLCOC_PROLOGUE
-  using G = Geo<PP>;
-  double2* tY = smem + warp * G::TILE;
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
+  C* tY = smem + warp * G::TILE;
   double d0 = 0.0, d1 = 0.0;
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    gather_rows<PP, false>(tY, a.A, a.W, nullptr, r0, p, lane, d0, d1);
+    gather_rows<PP, C, false>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, d0, d1);
     __syncwarp();
-    store_tile<PP>(a.V, tY, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.V), tY, r0, n, p, lane);
     __syncwarp();
   }
 }
 
 // bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): W_{m+1} = Q_m - U_m alpha'_m
 // (Q_m stored by the previous pass C); gram W^H W for the Cholesky QR.
-template <int PP>
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
-  BLCOC_PROLOGUE
-  using G = Geo<PP>;
-  double2* mA = smem;
-  double2* tiles = smem + (G::MATS_SMEM ? PP * PP : 0);
-  double2* tW = tiles + warp * 2 * G::TILE;
-  double2* tU = tW + G::TILE;
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
+  C* mA = smem;
+  C* tiles = smem + mats_off<PP, S>(1);
+  C* tW = tiles + warp * 2 * G::TILE;
+  C* tU = tW + G::TILE;
   if constexpr (G::MATS_SMEM) {
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> AL{G::MATS_SMEM ? mA : a.mats + M_ALPHA * PMAX * PMAX, p};
-  GramAcc<G::NTRI> g;
+  Fac<PP, S> AL{G::MATS_SMEM ? mA : reinterpret_cast<const C*>(a.mats + M_ALPHA * PMAX * PMAX), p};
+  GramAcc<G::NTRI, S> g;
   g.init(G_HERM, p, lane);
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    load_tile<PP>(tW, a.Q, r0, n, p, lane);
-    load_tile<PP>(tU, a.U, r0, n, p, lane);
+    load_tile<PP>(tW, blk<C>(a.Q), r0, n, p, lane);
+    load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
-    apply_full<PP, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
+    apply_full<PP, S, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
     __syncwarp();
     g.template add<true>(tW, tW, lane);
-    store_tile<PP>(a.W, tW, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
 }
 
 // bl_cocr_rq pass C (Algorithm 3, lines 5, 9, 10) with Q_{m+1} = W_{m+1} T_{m+1} (stored
 // for the next pass A):
 //   X_{m+1} = X_m + S_m (alpha'_m xi_m);  S_{m+1} = Q_{m+1} + S_m beta'_m;
 //   U_{m+1} = V_{m+1} + U_m beta'_m;  gram U^T U (next alpha').
-// flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.
-template <int PP>
+// flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.  flag&F_UEXPL: no U update
+// and no gram (U_{m+1} = A S_{m+1} is formed by the SpMM that follows).
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
-  BLCOC_PROLOGUE
-  using G = Geo<PP>;
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
   const bool first = a.flag & 1;
-  double2* mT = smem;
-  double2* mAX = smem + PP * PP;
-  double2* mB = smem + 2 * PP * PP;
-  double2* tiles = smem + (G::MATS_SMEM ? 3 * PP * PP : 0);
-  double2* b0 = tiles + warp * 3 * G::TILE;
-  double2* b1 = b0 + G::TILE;
-  double2* b2 = b1 + G::TILE;
+  const bool uexpl = a.flag & F_UEXPL;
+  C* mT = smem;
+  C* mAX = smem + PP * PP;
+  C* mB = smem + 2 * PP * PP;
+  C* tiles = smem + mats_off<PP, S>(3);
+  C* b0 = tiles + warp * 3 * G::TILE;
+  C* b1 = b0 + G::TILE;
+  C* b2 = b1 + G::TILE;
   if constexpr (G::MATS_SMEM) {
     load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
     load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
-  Fac<PP> AX{G::MATS_SMEM ? mAX : a.mats + M_ALPHAXI * PMAX * PMAX, p};
-  Fac<PP> BE{G::MATS_SMEM ? mB : a.mats + M_BETA * PMAX * PMAX, p};
-  GramAcc<G::NTRI> g;
+  Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
+  Fac<PP, S> AX{G::MATS_SMEM ? mAX : reinterpret_cast<const C*>(a.mats + M_ALPHAXI * PMAX * PMAX), p};
+  Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
+  GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    load_tile<PP>(b0, a.W, r0, n, p, lane);
+    load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
     if (!first) {
-      load_tile<PP>(b1, a.S, r0, n, p, lane);
-      load_tile<PP>(b2, a.X, r0, n, p, lane);
+      load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
+      load_tile<PP>(b2, blk<C>(a.X), r0, n, p, lane);
     }
     __syncwarp();
-    tri_apply_inplace<PP>(b0, T, p, lane);             // Q_{m+1}
+    tri_apply_inplace<PP, S>(b0, T, p, lane);             // Q_{m+1}
     __syncwarp();
-    store_tile<PP>(a.Q, b0, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.Q), b0, r0, n, p, lane);
     if (!first) {
-      apply_full<PP, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
+      apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
       __syncwarp();
-      store_tile<PP>(a.X, b2, r0, n, p, lane);
+      store_tile<PP>(blk<C>(a.X), b2, r0, n, p, lane);
       __syncwarp();
-      apply_full<PP, false>(b2, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
+      apply_full<PP, S, false>(b2, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
       __syncwarp();
-      store_tile<PP>(a.S, b2, r0, n, p, lane);
+      store_tile<PP>(blk<C>(a.S), b2, r0, n, p, lane);
     } else {
       __syncwarp();
-      store_tile<PP>(a.S, b0, r0, n, p, lane);
+      store_tile<PP>(blk<C>(a.S), b0, r0, n, p, lane);
     }
     __syncwarp();
-    load_tile<PP>(b1, a.V, r0, n, p, lane);
-    if (!first) load_tile<PP>(b2, a.U, r0, n, p, lane);
+    if (uexpl) continue;
+    load_tile<PP>(b1, blk<C>(a.V), r0, n, p, lane);
+    if (!first) load_tile<PP>(b2, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
     if (!first) {
-      apply_full<PP, false>(b1, b1, b2, BE, p, lane);  // U_{m+1} = V + U beta'
+      apply_full<PP, S, false>(b1, b1, b2, BE, p, lane);  // U_{m+1} = V + U beta'
       __syncwarp();
     }
     g.template add<false>(b1, b1, lane);
-    store_tile<PP>(a.U, b1, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.U), b1, r0, n, p, lane);
     __syncwarp();
   }
+  if (uexpl) return;
   __syncthreads();
-  cta_write_gram(g, tiles, a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
 }
 
 // bl_cocg_rq pass 1 (Algorithm 2, lines 5-6), Q_m stored by the previous pass 2:
 //   W_{m+1} = Q_m - (A S_m) alpha'_m;  X_{m+1} = X_m + S_m (alpha'_m xi_m);
 //   grams W^H W (QR) and W^T W (Q^T Q of line 7).  Partials: [W^H W tri][W^T W tri].
-template <int PP>
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
-  BLCOC_PROLOGUE
-  using G = Geo<PP>;
-  double2* mAX = smem;
-  double2* mA = smem + PP * PP;
-  double2* tiles = smem + (G::MATS_SMEM ? 2 * PP * PP : 0);
-  double2* b0 = tiles + warp * 3 * G::TILE;
-  double2* b1 = b0 + G::TILE;
-  double2* b2 = b1 + G::TILE;
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
+  C* mAX = smem;
+  C* mA = smem + PP * PP;
+  C* tiles = smem + mats_off<PP, S>(2);
+  C* b0 = tiles + warp * 3 * G::TILE;
+  C* b1 = b0 + G::TILE;
+  C* b2 = b1 + G::TILE;
   if constexpr (G::MATS_SMEM) {
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> AX{G::MATS_SMEM ? mAX : a.mats + M_ALPHAXI * PMAX * PMAX, p};
-  Fac<PP> AL{G::MATS_SMEM ? mA : a.mats + M_ALPHA * PMAX * PMAX, p};
-  GramAcc<G::NTRI> gh, gs;
+  Fac<PP, S> AX{G::MATS_SMEM ? mAX : reinterpret_cast<const C*>(a.mats + M_ALPHAXI * PMAX * PMAX), p};
+  Fac<PP, S> AL{G::MATS_SMEM ? mA : reinterpret_cast<const C*>(a.mats + M_ALPHA * PMAX * PMAX), p};
+  GramAcc<G::NTRI, S> gh, gs;
   gh.init(G_HERM, p, lane);
   gs.init(G_SYM, p, lane);
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    load_tile<PP>(b0, a.Q, r0, n, p, lane);
-    load_tile<PP>(b1, a.V, r0, n, p, lane);
+    load_tile<PP>(b0, blk<C>(a.Q), r0, n, p, lane);
+    load_tile<PP>(b1, blk<C>(a.V), r0, n, p, lane);
     __syncwarp();
-    apply_full<PP, true>(b0, b0, b1, AL, p, lane);     // W_{m+1} = Q_m - A S_m alpha'
+    apply_full<PP, S, true>(b0, b0, b1, AL, p, lane);     // W_{m+1} = Q_m - A S_m alpha'
     __syncwarp();
-    load_tile<PP>(b1, a.S, r0, n, p, lane);
-    load_tile<PP>(b2, a.X, r0, n, p, lane);
+    load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
+    load_tile<PP>(b2, blk<C>(a.X), r0, n, p, lane);
     __syncwarp();
-    apply_full<PP, false>(b2, b2, b1, AX, p, lane);    // X_{m+1}
+    apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);    // X_{m+1}
     gh.template add<true>(b0, b0, lane);
     gs.template add<false>(b0, b0, lane);
     __syncwarp();
-    store_tile<PP>(a.X, b2, r0, n, p, lane);
-    store_tile<PP>(a.W, b0, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.X), b2, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.W), b0, r0, n, p, lane);
     __syncwarp();
   }
   __syncthreads();
   double2* out = a.partials + (int64_t)blockIdx.x * a.ne;
-  cta_write_gram(gh, tiles, out, warp, lane);
-  cta_write_gram(gs, tiles, out + tri_count(p), warp, lane);
+  cta_write_gram(gh, reinterpret_cast<double2*>(tiles), out, warp, lane);
+  cta_write_gram(gs, reinterpret_cast<double2*>(tiles), out + tri_count(p), warp, lane);
 }
 
 // bl_cocg_rq pass 2 (Algorithm 2, line 8): Q_{m+1} = W_{m+1} T_{m+1} (stored for the next
 // pass 1), S_{m+1} = Q_{m+1} + S_m beta'_m.  flag=1 (setup, line 2): S_0 = Q_0 = W_0 T_0.
-template <int PP>
+template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
-  BLCOC_PROLOGUE
-  using G = Geo<PP>;
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
   const bool first = a.flag & 1;
-  double2* mT = smem;
-  double2* mB = smem + PP * PP;
-  double2* tiles = smem + (G::MATS_SMEM ? 2 * PP * PP : 0);
-  double2* b0 = tiles + warp * 2 * G::TILE;
-  double2* b1 = b0 + G::TILE;
+  C* mT = smem;
+  C* mB = smem + PP * PP;
+  C* tiles = smem + mats_off<PP, S>(2);
+  C* b0 = tiles + warp * 2 * G::TILE;
+  C* b1 = b0 + G::TILE;
   if constexpr (G::MATS_SMEM) {
     load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP> T{G::MATS_SMEM ? mT : a.mats + M_TINV * PMAX * PMAX, p};
-  Fac<PP> BE{G::MATS_SMEM ? mB : a.mats + M_BETA * PMAX * PMAX, p};
+  Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
+  Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
   for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    load_tile<PP>(b0, a.W, r0, n, p, lane);
-    if (!first) load_tile<PP>(b1, a.S, r0, n, p, lane);
+    load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
+    if (!first) load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
     __syncwarp();
-    tri_apply_inplace<PP>(b0, T, p, lane);            // Q_{m+1}
+    tri_apply_inplace<PP, S>(b0, T, p, lane);            // Q_{m+1}
     __syncwarp();
-    store_tile<PP>(a.Q, b0, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.Q), b0, r0, n, p, lane);
     __syncwarp();
-    if (!first) apply_full<PP, false>(b0, b0, b1, BE, p, lane);
+    if (!first) apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);
     __syncwarp();
-    store_tile<PP>(a.S, b0, r0, n, p, lane);
+    store_tile<PP>(blk<C>(a.S), b0, r0, n, p, lane);
     __syncwarp();
+  }
+}
+
+// Refinement update of the mixed-precision form: X (FP64) += D (working precision, held
+// in a.V), elementwise over the n x p block.
+template <int PP, typename S>
+__global__ void __launch_bounds__(256) k_axpy(const PassArgs a) {
+  using C = typename Cx<S>::T;
+  const int64_t total = a.A.n * a.p;
+  const C* D = blk<C>(a.V);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const C d = D[e];
+    double2 x = a.X[e];
+    x.x += (double)d.x;
+    x.y += (double)d.y;
+    a.X[e] = x;
   }
 }
 
 #undef BLCOC_PROLOGUE
 
 // ---------------------------------------------------------------------------------- launch
-enum PassKind { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_NKIND };
+enum PassKind { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_AXPY, K_NKIND };
 
-template <int PP>
+template <int PP, typename S>
 constexpr size_t pass_smem(int kind) {
-  using G = Geo<PP>;
-  const size_t mat = (size_t)PP * PP * sizeof(double2);
-  const size_t tile = (size_t)G::TILE * sizeof(double2);
-  const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2};
-  const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2};
-  return (G::MATS_SMEM ? nmats[kind] * mat : 0) + (size_t)NWARP * ntiles[kind] * tile;
+  using G = Geo<PP, S>;
+  const size_t esz = sizeof(typename Cx<S>::T);
+  const size_t tile = (size_t)G::TILE * esz;
+  const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2, 0};
+  const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2, 0};
+  if (kind == K_RESID) return (size_t)NWARP * PP * CHUNK * sizeof(double2);   // FP64 residual tile
+  const size_t mats = (size_t)mats_off<PP, S>(nmats[kind]) * esz;
+  size_t s = mats + (size_t)NWARP * ntiles[kind] * tile;
+  // the CTA-level Gram reduction reuses the tile area: NWARP * E double2 (two Grams at most
+  // are written one after the other, so one E-sized area suffices)
+  const size_t red = (size_t)NWARP * tri_count(PP) * sizeof(double2);
+  const bool has_gram = kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1;
+  if (has_gram && s < mats + red) s = mats + red;
+  return s;
 }
 
-template <int PP>
+template <int PP, typename S>
 int pass_grid(int64_t n, int kind, int num_sms) {
-  const size_t smem = pass_smem<PP>(kind);
+  if (kind == K_AXPY) return num_sms * 4;
+  const size_t smem = pass_smem<PP, S>(kind);
   int per_sm = (int)((227u * 1024u) / (smem + 1024u));
   per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
   const int64_t nchunks = (n + CHUNK - 1) / CHUNK;
@@ -611,40 +705,47 @@ int pass_grid(int64_t n, int kind, int num_sms) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <int PP, int KIND, void (*K)(const PassArgs)>
+template <int PP, typename S, int KIND, void (*K)(const PassArgs)>
 void launch_pass(const PassArgs& a, cudaStream_t s) {
-  K<<<a.grid, NWARP * 32, pass_smem<PP>(KIND), s>>>(a);
+  if constexpr (KIND == K_AXPY) K<<<a.grid, 256, 0, s>>>(a);
+  else K<<<a.grid, NWARP * 32, pass_smem<PP, S>(KIND), s>>>(a);
 }
 
-template <int PP>
+template <int PP, typename S>
 void prepare_pass_kernels() {
   static bool done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || done[dev]) return;
-  cudaFuncSetAttribute(k_resid<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_RESID));
-  cudaFuncSetAttribute(k_spmm_gram<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_SPMM_GRAM));
-  cudaFuncSetAttribute(k_spmm_plain<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<PP>(K_SPMM_PLAIN));
-  cudaFuncSetAttribute(k_cocr_passA<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCR_A));
-  cudaFuncSetAttribute(k_cocr_passC<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCR_C));
-  cudaFuncSetAttribute(k_cocg_pass1<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCG_1));
-  cudaFuncSetAttribute(k_cocg_pass2<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP>(K_COCG_2));
+  cudaFuncSetAttribute(k_resid<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP, S>(K_RESID));
+  cudaFuncSetAttribute(k_spmm_gram<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, S>(K_SPMM_GRAM));
+  cudaFuncSetAttribute(k_spmm_plain<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, S>(K_SPMM_PLAIN));
+  cudaFuncSetAttribute(k_cocr_passA<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, S>(K_COCR_A));
+  cudaFuncSetAttribute(k_cocr_passC<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, S>(K_COCR_C));
+  cudaFuncSetAttribute(k_cocg_pass1<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, S>(K_COCG_1));
+  cudaFuncSetAttribute(k_cocg_pass2<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, S>(K_COCG_2));
   done[dev] = true;
 }
 
-template <int PP>
+template <int PP, typename S>
 const KernelSet& kernel_set() {
   static const KernelSet ks = {
-      &launch_pass<PP, K_RESID, k_resid<PP>>,
-      &launch_pass<PP, K_SPMM_GRAM, k_spmm_gram<PP>>,
-      &launch_pass<PP, K_SPMM_PLAIN, k_spmm_plain<PP>>,
-      &launch_pass<PP, K_COCR_A, k_cocr_passA<PP>>,
-      &launch_pass<PP, K_COCR_C, k_cocr_passC<PP>>,
-      &launch_pass<PP, K_COCG_1, k_cocg_pass1<PP>>,
-      &launch_pass<PP, K_COCG_2, k_cocg_pass2<PP>>,
-      &pass_grid<PP>,
-      &prepare_pass_kernels<PP>,
+      &launch_pass<PP, S, K_RESID, k_resid<PP, S>>,
+      &launch_pass<PP, S, K_SPMM_GRAM, k_spmm_gram<PP, S>>,
+      &launch_pass<PP, S, K_SPMM_PLAIN, k_spmm_plain<PP, S>>,
+      &launch_pass<PP, S, K_COCR_A, k_cocr_passA<PP, S>>,
+      &launch_pass<PP, S, K_COCR_C, k_cocr_passC<PP, S>>,
+      &launch_pass<PP, S, K_COCG_1, k_cocg_pass1<PP, S>>,
+      &launch_pass<PP, S, K_COCG_2, k_cocg_pass2<PP, S>>,
+      &launch_pass<PP, S, K_AXPY, k_axpy<PP, S>>,
+      &pass_grid<PP, S>,
+      &prepare_pass_kernels<PP, S>,
   };
   return ks;
 }

@@ -310,15 +310,20 @@ __device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s
 
 // Setup after the residual pass: ||B||_F, Q_0 xi_0 = R_0 (Cholesky QR), T_0 = xi_0^{-1};
 // cocg: G_QQ = Q_0^T Q_0 = T^T (R^T R) T.
-__global__ void k_small_setup(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+// inner = 1 (refinement step): the stopping test is relative to ||R_0||_F, the norm of
+// this solve's right-hand side, which is the outer residual.
+__global__ void k_small_setup(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
+                              int inner) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   sum_stage1(stage1, ncomp, S.gs);
   const int E = tri_count(p);
-  const double sb = S.gs[2 * (2 * E)];
+  const double sb = inner ? S.gs[2 * (2 * E) + 1] : S.gs[2 * (2 * E)];
   if (threadIdx.x == 0) {
     ctrl->sumsq_b = sb;
     ctrl->nb = sqrt(sb);
+    ctrl->trr = sqrt(S.gs[2 * (2 * E) + 1]);
+    ctrl->pad[0] = S.gs[2 * (2 * E)];   // sum |B|^2
   }
   if (!(sb > 0.0) || !isfinite(sb)) {
     if (threadIdx.x == 0) {
@@ -548,7 +553,8 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
   const size_t sm = small_smem();
   const int ncomp = 2 * ne;
   switch (kind) {
-    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl); break;
+    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl, 0); break;
+    case SK_SETUP_INNER: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl, 1); break;
     case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
     case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist); break;
     case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl); break;

@@ -4,7 +4,7 @@
 
 namespace blcoc {
 
-enum SmallKind { SK_SETUP = 0, SK_COCR_H0, SK_ALPHA, SK_CHOL, SK_COCR_BETA, SK_TRR };
+enum SmallKind { SK_SETUP = 0, SK_COCR_H0, SK_ALPHA, SK_CHOL, SK_COCR_BETA, SK_TRR, SK_SETUP_INNER };
 
 void prepare_small_kernels();
 // ctrl == nullptr: run even after the solve has finished (final residual pass).

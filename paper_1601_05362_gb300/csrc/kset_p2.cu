@@ -1,5 +1,6 @@
-// Instantiation of the row-pass kernels for block width 2.
+// Instantiation of the row-pass kernels for block width 2 (FP64 and complex64).
 #include "blcoc_rowpass.cuh"
 namespace blcoc {
-template const KernelSet& kernel_set<2>();
+template const KernelSet& kernel_set<2, double>();
+template const KernelSet& kernel_set<2, float>();
 }

@@ -198,3 +198,25 @@ def test_device_csr_input():
     Y = torch.zeros_like(X)
     h.spmm(X, Y)
     assert rel(Y.cpu().numpy(), A.to_scipy() @ Xh) < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 4, 16])
+def test_cocr_explicit_u_option_matches_oracle(p):
+    """Option u_explicit = 1 forms U_{m+1} = A S_{m+1} by a sparse product instead of
+    Algorithm 3's recurrence; the iterates are the same in exact arithmetic."""
+    torch = need_gpu()
+    n = 1500 + 3 * p
+    A = P.random_complex_symmetric(n, 8, seed=100 + p, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(n, p, 200 + p)
+    ref = O.bl_cocr_rq(A.to_scipy(), Bh, tol=0.0, maxit=12)
+    h = _handle(A)
+    h.set_option("u_explicit", 1)
+    B = to_dev(torch, Bh)
+    X = torch.zeros_like(B)
+    assert h.solve(B, X, tol=0.0, maxit=12) == 5
+    hist = h.info()["hist"]
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
+    assert rel(X.cpu().numpy(), ref.X) < X_TOL
+    X.zero_()
+    assert h.solve(B, X, tol=1e-10, maxit=2000) == 0
+    assert h.info()["relres_true"] < 1e-9
