@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--method", choices=["cocr_rq", "cocg_rq"], default="cocr_rq")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="profiler case: one solve of the same workload for exactly ITERS iterations, then exit")
     return ap.parse_args()
@@ -183,6 +184,97 @@ def run_cpu_sample(method, iters):
     d = json.loads(out.stdout.strip().splitlines()[-1])
     d["cores"] = cores
     return d
+
+
+# ----------------------------------------------------------------------------- variants
+def _timed_solves(h, B, X, method, tol, maxit, reps, stream):
+    import torch
+    ms, iters, trr = [], [], []
+    for _ in range(reps):
+        X.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = h.solve(B, X, method=method, tol=tol, maxit=maxit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        info = h.info(hist_len=1)
+        iters.append(info["iters"])
+        trr.append(info["relres_true"])
+    from paper_1601_05362_gb300 import blcoc
+    return {"status": blcoc.status_string(st), "ms_per_solve": statistics.median(ms), "iters": iters[-1],
+            "relres_true": trr[-1]}
+
+
+def run_variants(h, B, X, pr, args, stream):
+    """Same-run measurements next to the headline (not part of it): Algorithm 3 with
+    U_{m+1} = A S_{m+1} formed by a second sparse product, on the headline workload; and
+    the mixed-precision refinement against plain FP64 on the 27-point random complex
+    symmetric family (n = 262,144, p = 16), where complex64 inner solves converge."""
+    import torch
+    from paper_1601_05362_gb300 import blcoc, problems as P
+    out = {}
+    h.set_option("u_explicit", 1)
+    _timed_solves(h, B, X, args.method, TOL, MAXIT, 1, stream)
+    r = _timed_solves(h, B, X, args.method, TOL, MAXIT, 2, stream)
+    h.set_option("u_explicit", 0)
+    r["value"] = pr.p / (r["ms_per_solve"] / 1e3)
+    r["unit"] = UNIT
+    r["workload"] = WORKLOAD
+    out["cocr_rq_explicit_U"] = r
+    A2 = P.random_symmetric_27pt(64, 64, 64, seed=2)
+    B2 = torch.from_numpy(P.complex_normal(A2.n, 16, 5)).cuda()
+    X2 = torch.zeros_like(B2)
+    with blcoc.Handle.from_csr(A2) as h2:
+        for name, meth in (("fp64_cocr_rq", "cocr_rq"), ("mixed_cocr_rq", "cocr_rq_mixed")):
+            _timed_solves(h2, B2, X2, meth, TOL, MAXIT, 1, stream)
+            r = _timed_solves(h2, B2, X2, meth, TOL, MAXIT, 3, stream)
+            if meth.endswith("mixed"):
+                r["outer_iters"] = h2.stat("outer_iters")
+            r["value"] = 16 / (r["ms_per_solve"] / 1e3)
+            r["unit"] = UNIT
+            r["workload"] = "random27pt_64cube_p16 (27-point pattern, 10% pairs dropped, diag 4+0.5i)"
+            out[name + "_random27pt"] = r
+    out["autograd_random27pt_n1048576_p8"] = run_autograd_variant(stream)
+    return out
+
+
+def run_autograd_variant(stream):
+    """Differentiable solve on the 27-point random family at n = 1,048,576 (128x128x64),
+    p = 8, loss sum |C^T X|^2: forward solve, then forward + backward (adjoint solve +
+    sampled outer product), both to 1e-10; CUDA-event times."""
+    import torch
+    from paper_1601_05362_gb300 import problems as P
+    from paper_1601_05362_gb300.autograd import SymmetricCSR, blcoc_solve
+    A = P.random_symmetric_27pt(128, 128, 64, seed=2)
+    op = SymmetricCSR(A.row_ptr, A.col_idx, A.n, A.vals)
+    B = torch.from_numpy(P.complex_normal(A.n, 8, 3)).cuda()
+    Cm = torch.from_numpy(P.complex_normal(A.n, 8, 4)).cuda()
+    vals0 = torch.from_numpy(A.vals).cuda()
+
+    def once(backward):
+        vals = vals0.clone().requires_grad_(backward)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        X = blcoc_solve(vals, B, op, tol=1e-10, maxit=5000)
+        L = (Cm.transpose(0, 1) @ X).abs().pow(2).sum()
+        if backward:
+            L.backward()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), op.handle.info(hist_len=1)["iters"]
+
+    once(True)
+    fwd = [once(False) for _ in range(2)]
+    both = [once(True) for _ in range(2)]
+    op.close()
+    return {"n": A.n, "nnz": A.nnz, "p": 8, "forward_ms": min(f[0] for f in fwd),
+            "forward_backward_ms": min(b[0] for b in both), "forward_iters": fwd[-1][1],
+            "adjoint_iters": both[-1][1]}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -341,6 +433,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if not args.no_variants:
+        line["variants"] = run_variants(h, B, X, pr, args, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             d = run_cpu_sample(args.method, 4)

@@ -129,6 +129,25 @@ blcoc_status blcoc_spmm(blcoc_handle h, const void* X, void* Y, int p);
 blcoc_status blcoc_residual_norm(blcoc_handle h, const void* B, const void* X, int p, double* out);
 
 /*
+ * blcoc_set_values - replace the values of A, keeping its pattern (for example between
+ * optimisation steps of the differentiable solve).  vals: nnz complex values in the
+ * order of the handle's col_idx; host_ptrs as in blcoc_create.  The symmetry check of
+ * blcoc_create is repeated; on BLCOC_ERR_NOT_SYMMETRIC the handle holds the new values
+ * and must not be used for solves until valid values are set.
+ */
+blcoc_status blcoc_set_values(blcoc_handle h, const void* vals, int host_ptrs);
+
+/*
+ * blcoc_sampled_grad - the gradient of a real loss through X = A^{-1} B with respect to
+ * the stored values of A: grad_vals[e] = - sum_k Lambda[i][k] conj(X[j][k]) for entry e
+ * at (i, j), where Lambda = A^{-H} G is the adjoint solution for the upstream gradient G
+ * (conjugate-Wirtinger convention; with A = A^T, Lambda = conj(A^{-1} conj(G)), one more
+ * solve with the same A).  Lambda, X: n x p device blocks; grad_vals: nnz device values.
+ * The paper defines the solve (Sec. 1, Eq. 1.1); its derivative is standard calculus.
+ */
+blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* X, int p, void* grad_vals);
+
+/*
  * blcoc_set_option - tuning switches (key, value):
  *   "graph"      : 1 (default) replays the iteration as a CUDA graph, 0 launches kernels.
  *   "poll"       : iterations between two host checks of the convergence flag (default 16).

@@ -177,12 +177,14 @@ def bl_cocg_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
     return Result(X=X, hist=hist, iters=m, status=status, xi=xi, record=rec if record else {})
 
 
-def bl_cocr_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False, alpha_rhs="QV") -> Result:
+def bl_cocr_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False, alpha_rhs="QV", u_explicit=False) -> Result:
     """Block COCR with residual orthonormalization, Algorithm 3 (Sec. 2.2).
 
     ``alpha_rhs`` selects the right-hand side of the alpha' system (line 4): ``"QV"``
     (``Q_m^T V_m``, derived from Algorithm 1, default) or ``"QU"`` (``Q_m^T U_m``, as
-    printed)."""
+    printed).  ``u_explicit`` replaces line 10's recurrence ``U_{m+1} = V_{m+1} + U_m
+    beta'_m`` by the product ``U_{m+1} = A S_{m+1}`` it stands for (Sec. 2.1 introduces
+    the recurrence only to save that product)."""
     if alpha_rhs not in ("QV", "QU"):
         raise ValueError("alpha_rhs must be 'QV' or 'QU'")
     B = np.asarray(B, dtype=np.complex128)
@@ -228,7 +230,7 @@ def bl_cocr_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False, alpha_rhs="QV
             status, m = BREAKDOWN, m + 1
             break
         S = Qn + S @ beta                                 # line 9
-        U = Vn + U @ beta                                 # line 10
+        U = (A @ S) if u_explicit else (Vn + U @ beta)    # line 10
         Q, V = Qn, Vn
     return Result(X=X, hist=hist, iters=m, status=status, xi=xi, record=rec if record else {})
 

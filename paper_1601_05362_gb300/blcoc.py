@@ -46,6 +46,8 @@ SIGNATURES = {
     "blcoc_get_stat": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(C.c_int64)]),
     "blcoc_residual_norm_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "blcoc_set_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "blcoc_sampled_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "blcoc_destroy": (C.c_int, [C.c_void_p]),
     "blcoc_status_string": (C.c_char_p, [C.c_int]),
     "blcoc_last_error": (C.c_char_p, [C.c_void_p]),
@@ -89,6 +91,9 @@ def _ptr(x):
         if isinstance(x, torch.Tensor):
             if not x.is_contiguous():
                 raise ValueError("tensor must be contiguous")
+            if x.is_complex() and (x.is_conj() or x.is_neg()):
+                # a lazy conjugate / negative view: its memory does not hold its values
+                raise ValueError("tensor is a lazy conj/neg view; pass x.resolve_conj() / x.conj_physical()")
             return x.data_ptr(), x
     except ImportError:  # pragma: no cover
         pass
@@ -210,6 +215,29 @@ class Handle:
         if st != BLCOC_OK:
             raise BlcocError(st, self.last_error())
         return out.value
+
+    def set_values(self, vals):
+        """Replace A's values (same pattern); torch device tensor or host array."""
+        if len(vals) != self.nnz:
+            raise ValueError("vals must have nnz entries")
+        dev = _is_cuda(vals)
+        if not dev:
+            vals = np.ascontiguousarray(vals, dtype=np.complex128)
+        pv, kv = _ptr(vals)
+        st = self._lib.blcoc_set_values(self._h, pv, 0 if dev else 1)
+        if st != BLCOC_OK:
+            raise BlcocError(st, self.last_error())
+
+    def sampled_grad(self, Lam, X, out):
+        """out[e] = -sum_k Lam[i,k] conj(X[j,k]) over the stored entries (device tensors)."""
+        _check_block(Lam, self.n, "Lambda")
+        _check_block(X, self.n, "X")
+        pl, kl = _ptr(Lam)
+        px, kx = _ptr(X)
+        po, ko = _ptr(out)
+        st = self._lib.blcoc_sampled_grad(self._h, pl, px, int(X.shape[1]), po)
+        if st != BLCOC_OK:
+            raise BlcocError(st, self.last_error())
 
     def set_option(self, key: str, value: int):
         st = self._lib.blcoc_set_option(self._h, key.encode(), int(value))

@@ -529,6 +529,46 @@ blcoc_status blcoc_create(blcoc_handle* out, int64_t n, int64_t nnz, const int32
   return BLCOC_OK;
 }
 
+blcoc_status blcoc_set_values(blcoc_handle h, const void* vals, int host_ptrs) {
+  if (!h || !vals) return invalid(h, "NULL argument");
+  CK(h, cudaSetDevice(h->dev));
+  CK(h, cudaEventRecord(h->ev, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
+  CK(h, cudaMemcpyAsync(h->va, vals, h->nnz * sizeof(double2),
+                        host_ptrs ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->s));
+  CK(h, cudaMemsetAsync(h->flags, 0, 4 * sizeof(int), h->s));
+  launch_validate(h->n, h->nnz, h->rp, h->ci, h->va, h->flags, 1, h->s);
+  CK(h, cudaGetLastError());
+  int hf[4] = {0, 0, 0, 0};
+  CK(h, cudaMemcpyAsync(hf, h->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(h, cudaStreamSynchronize(h->s));
+  if (hf[1] != 0) {
+    h->err = "A is not symmetric: some |a_ij - a_ji| > 1e-12 max(|a_ij|, |a_ji|)";
+    return BLCOC_ERR_NOT_SYMMETRIC;
+  }
+  if (h->vaf) {   // keep the complex64 copy in step
+    k_vals_to_c64<<<h->num_sms * 4, 256, 0, h->s>>>(h->va, h->vaf, h->nnz);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->s));
+  }
+  return BLCOC_OK;
+}
+
+blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* X, int p, void* grad_vals) {
+  if (!h || !Lambda || !X || !grad_vals) return invalid(h, "NULL argument");
+  if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
+  CK(h, cudaSetDevice(h->dev));
+  CK(h, cudaEventRecord(h->ev, h->user_stream));
+  CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
+  launch_sampled_grad(h->n, h->rp, h->ci, (const double2*)Lambda, (const double2*)X, p, (double2*)grad_vals,
+                      h->num_sms, h->s);
+  CK(h, cudaGetLastError());
+  CK(h, cudaEventRecord(h->ev, h->s));
+  CK(h, cudaStreamWaitEvent(h->user_stream, h->ev, 0));
+  CK(h, cudaStreamSynchronize(h->s));
+  return BLCOC_OK;
+}
+
 blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
   if (!h || !key) return invalid(h, "NULL handle or key");
   if (!strcmp(key, "graph")) {

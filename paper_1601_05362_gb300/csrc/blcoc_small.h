@@ -11,6 +11,8 @@ void prepare_small_kernels();
 void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s);
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
                   double* hist, cudaStream_t s);
+void launch_sampled_grad(int64_t n, const int* rp, const int* ci, const double2* Lam, const double2* X, int p,
+                         double2* out, int num_sms, cudaStream_t s);
 void launch_validate(int64_t n, int64_t nnz, const int* rp, const int* ci, const double2* va, int* flags, int which,
                      cudaStream_t s);
 

@@ -57,3 +57,13 @@ def test_binding_fails_loudly_without_library(tmp_path):
             blcoc.load_library(str(tmp_path / "missing.so"))
         finally:
             blcoc._lib = saved
+
+
+def test_binding_rejects_lazy_conjugate_views():
+    """The C ABI reads raw memory; a torch conj()/neg view does not hold its values there."""
+    torch = pytest.importorskip("torch")
+    from paper_1601_05362_gb300 import blcoc
+    x = torch.zeros((4, 2), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="lazy conj"):
+        blcoc._ptr(x.conj())
+    blcoc._ptr(x.conj_physical())

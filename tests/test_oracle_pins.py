@@ -386,3 +386,16 @@ def test_golden_fixture_is_reproduced():
         assert r.iters == ref["iters"] and r.status == ref["status"]
         h = np.array(r.hist[:20]); hr = np.array(ref["hist"][:20])
         assert np.max(np.abs(h - hr) / hr) < 1e-12
+
+
+def test_cocr_rq_explicit_u_equals_galerkin():
+    """U_{m+1} = A S_{m+1} instead of the recurrence gives the same iterates (Sec. 2.1)."""
+    n, p = 40, 2
+    A = dense_cs(n, seed=17)
+    rng = np.random.default_rng(18)
+    B = rng.standard_normal((n, p)) + 1j * rng.standard_normal((n, p))
+    X0 = np.zeros_like(B)
+    for m in range(1, 5):
+        r = O.bl_cocr_rq(A, B, X0=X0, tol=0.0, maxit=m, u_explicit=True)
+        Xg = galerkin_iterate(A, B, X0, m, "cocr")
+        assert np.linalg.norm(r.X - Xg) / np.linalg.norm(Xg) < 1e-9
