@@ -54,7 +54,18 @@ typedef enum {
  * then on the true residual ||B - A X||_F / ||B||_F and maxit bounds the total inner
  * iterations; blcoc_get_info returns the inner iteration count and, as hist, the true
  * relative residual after each refinement step. */
-typedef enum { BLCOC_COCG_RQ = 0, BLCOC_COCR_RQ = 1, BLCOC_COCG_RQ_MIXED = 2, BLCOC_COCR_RQ_MIXED = 3 } blcoc_method;
+/* BLCOC_COCR is the plain block COCR of Algorithm 1 (Sec. 2.1) and BLCOC_COCG the plain
+ * block COCG (Sec. 2.1, Eqs. 2.1-2.2 with Table 1's COCG conditions:
+ * alpha = (P^T A P)^{-1} R^T R, beta = (R_m^T R_m)^{-1} R_{m+1}^T R_{m+1}); both stop when
+ * ||R_m||_F / ||B||_F <= tol (Algorithm 1 normalises by ||R_0||_F, equal for X0 = 0). */
+typedef enum {
+  BLCOC_COCG_RQ = 0,
+  BLCOC_COCR_RQ = 1,
+  BLCOC_COCG_RQ_MIXED = 2,
+  BLCOC_COCR_RQ_MIXED = 3,
+  BLCOC_COCG = 4,
+  BLCOC_COCR = 5
+} blcoc_method;
 
 /* Largest number of right-hand sides one solve accepts. */
 #define BLCOC_MAX_P 32

@@ -28,9 +28,11 @@ BLCOC_COCG_RQ = 0
 BLCOC_COCR_RQ = 1
 BLCOC_COCG_RQ_MIXED = 2
 BLCOC_COCR_RQ_MIXED = 3
+BLCOC_COCG = 4
+BLCOC_COCR = 5
 BLCOC_MAX_P = 32
 METHODS = {"cocg_rq": BLCOC_COCG_RQ, "cocr_rq": BLCOC_COCR_RQ, "cocg_rq_mixed": BLCOC_COCG_RQ_MIXED,
-           "cocr_rq_mixed": BLCOC_COCR_RQ_MIXED}
+           "cocr_rq_mixed": BLCOC_COCR_RQ_MIXED, "cocg": BLCOC_COCG, "cocr": BLCOC_COCR}
 
 # name -> (restype, argtypes) for every symbol include/blcoc.h declares
 SIGNATURES = {

@@ -312,10 +312,11 @@ struct Solver {
     timed_end(t);
     ++launches;
   }
+  int plain = 0;   // 1: plain block method (Algorithm 1 / derived block COCG)
   void small(SmallKind k, int ne) {
     Timer t;
     timed_begin(t, kKindSmall0 + (int)k);
-    launch_small(k, p, method, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s);
+    launch_small(k, p, method + 16 * plain, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s);
     timed_end(t);
     ++launches;
   }
@@ -864,7 +865,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   h->err.clear();
   if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
   if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ && method != BLCOC_COCG_RQ_MIXED &&
-      method != BLCOC_COCR_RQ_MIXED)
+      method != BLCOC_COCR_RQ_MIXED && method != BLCOC_COCG && method != BLCOC_COCR)
     return invalid(h, "unknown method");
   if (!(tol >= 0.0) || std::isinf(tol)) return invalid(h, "tol must be finite and >= 0");
   if (maxit < 0) return invalid(h, "maxit must be >= 0");
@@ -911,11 +912,14 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
     return solve_mixed(h, dB, dX, X, hostX, p, method == BLCOC_COCR_RQ_MIXED ? BLCOC_COCR_RQ : BLCOC_COCG_RQ, tol,
                        maxit);
 
+  const bool plain = method == BLCOC_COCG || method == BLCOC_COCR;
+  const int base_method = plain ? (method == BLCOC_COCR ? BLCOC_COCR_RQ : BLCOC_COCG_RQ) : (int)method;
   int PP = 0;
-  Solver sv{h, kernels_for(p, &PP), PP, p, (int)method, dB, dX};
+  Solver sv{h, kernels_for(p, &PP), PP, p, base_method, dB, dX};
   sv.K->prepare();
   sv.use_fp64_blocks();
-  sv.uexpl = h->u_explicit != 0;
+  sv.plain = plain ? 1 : 0;
+  sv.uexpl = !plain && h->u_explicit != 0;
   Ctrl c0{};
   c0.maxit = maxit;
   c0.tol = tol;
@@ -931,7 +935,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   } else if (!h->h_ctrl->done) {
     sv.setup_rest();
     CK(h, cudaGetLastError());
-    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0), maxit);
+    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain, maxit);
     if (st != BLCOC_OK) return st;
   }
   // true residual of the returned iterate

@@ -313,7 +313,7 @@ __device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s
 // inner = 1 (refinement step): the stopping test is relative to ||R_0||_F, the norm of
 // this solve's right-hand side, which is the outer residual.
 __global__ void k_small_setup(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                              int inner) {
+                              int inner, int plain) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   sum_stage1(stage1, ncomp, S.gs);
@@ -329,6 +329,22 @@ __global__ void k_small_setup(int p, int method, const double* stage1, int ncomp
     if (threadIdx.x == 0) {
       ctrl->done = (sb == 0.0) ? 1 : 3;
       ctrl->bd_code = (sb == 0.0) ? 0 : 5;
+    }
+    return;
+  }
+  if (plain) {
+    // plain block methods (Algorithm 1, derived block COCG): no orthonormalisation, so
+    // tau = T = xi = I and the row passes reduce to the plain recurrences
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+      const double2 v = (e / p == e % p) ? make_double2(1.0, 0.0) : cz();
+      slot(mats, M_XI)[e] = v;
+      slot(mats, M_TAU)[e] = v;
+      slot(mats, M_TINV)[e] = v;
+    }
+    if (threadIdx.x == 0) ctrl->pad[1] = S.gs[2 * (2 * E) + 1];   // ||R_0||_F^2
+    if (method == 0) {
+      expand_tri(S.gs + 2 * E, S.m[3], p, false);
+      gstore(slot(mats, M_H), S.m[3], p);                       // R_0^T R_0
     }
     return;
   }
@@ -363,12 +379,14 @@ __global__ void k_small_cocr_H0(int p, const double* stage1, int ncomp, double2*
 // Top of iteration m (Algorithms 2-3, lines 3-4): record ||xi_m||_F/||B||_F, stop if
 // <= tol or m = maxit; else alpha'_m = G1^{-1} RHS with G1 = U^T U (cocr) or S^T A S
 // (cocg) and RHS = Q^T V (cocr) or Q^T Q (cocg); also alpha'_m xi_m.
-__global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, double* hist) {
+// plain: the stopping test uses ||R_m||_F (Algorithm 1) recorded by the previous stage.
+__global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, double* hist,
+                              int plain) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   const int m = ctrl->iter;
   gload(S.m[0], slot(mats, M_XI), p);
-  const double rel = fro_norm(S.m[0], p, S.red) / ctrl->nb;
+  const double rel = (plain ? sqrt(ctrl->pad[1]) : fro_norm(S.m[0], p, S.red)) / ctrl->nb;
   if (threadIdx.x == 0) {
     hist[m] = rel;
     ctrl->relres = rel;
@@ -402,10 +420,35 @@ __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* m
 // After W_{m+1} (Algorithms 2-3, line 6): Cholesky QR tau, T = tau^{-1},
 // xi_{m+1} = tau xi_m.  cocg also does line 7: G_QQ+ = T^T (W^T W) T and
 // beta' = G_QQ^{-1} tau^T G_QQ+.
-__global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+// plain: no QR; record ||R_{m+1}||_F^2 (trace of the Hermitian Gram) and, for block COCG,
+// beta = (R_m^T R_m)^{-1} R_{m+1}^T R_{m+1}.
+__global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
+                             int plain) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   sum_stage1(stage1, ncomp, S.gs);
+  if (plain) {
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0, e = 0; i < p; e += p - i, ++i) t += S.gs[2 * e];   // diagonal entries of the triangle
+      ctrl->pad[1] = t;
+    }
+    if (method == 0) {
+      const int E = tri_count(p);
+      expand_tri(S.gs + 2 * E, S.m[0], p, false);      // R_{m+1}^T R_{m+1}
+      gload(S.m[3], slot(mats, M_H), p);                // R_m^T R_m
+      for (int e = threadIdx.x; e < p * p; e += blockDim.x) S.m[4][(e / p) * LD + e % p] = S.m[0][(e / p) * LD + e % p];
+      __syncthreads();
+      gstore(slot(mats, M_H), S.m[0], p);
+      if (!lu_solve(S.m[3], S.m[4], p, p, S.red, S.ish)) {
+        if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 4; }
+        return;
+      }
+      gstore(slot(mats, M_BETA), S.m[4], p);
+    }
+    __syncthreads();
+    return;
+  }
   expand_tri(S.gs, S.m[0], p, true);
   if (!chol_upper(S.m[0], S.m[1], p, S.red)) {
     if (threadIdx.x == 0) {
@@ -552,12 +595,15 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
                   double* hist, cudaStream_t s) {
   const size_t sm = small_smem();
   const int ncomp = 2 * ne;
+  const int m = method & 15, plain = (method >> 4) & 1;   // method: 0 cocg / 1 cocr, +16 plain form
   switch (kind) {
-    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl, 0); break;
-    case SK_SETUP_INNER: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl, 1); break;
+    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, plain); break;
+    case SK_SETUP_INNER:
+      k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, plain);
+      break;
     case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
-    case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist); break;
-    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, method, stage1, ncomp, mats, ctrl); break;
+    case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain); break;
+    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain); break;
     case SK_COCR_BETA: k_small_cocr_beta<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
     case SK_TRR: k_small_trr<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, ctrl); break;
   }

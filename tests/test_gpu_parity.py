@@ -220,3 +220,50 @@ def test_cocr_explicit_u_option_matches_oracle(p):
     X.zero_()
     assert h.solve(B, X, tol=1e-10, maxit=2000) == 0
     assert h.info()["relres_true"] < 1e-9
+
+
+@pytest.mark.parametrize("method", ["cocg", "cocr"])
+@pytest.mark.parametrize("p", [1, 3, 8, 16])
+def test_plain_block_methods_match_oracle(method, p):
+    """Plain block COCR (Algorithm 1) and plain block COCG against the oracle's plain forms."""
+    torch = need_gpu()
+    n = 1500 + 3 * p
+    A = P.random_complex_symmetric(n, 8, seed=300 + p, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(n, p, 400 + p)
+    f = O.bl_cocg if method == "cocg" else O.bl_cocr
+    ref = f(A.to_scipy(), Bh, tol=0.0, maxit=10)
+    h = _handle(A)
+    B = to_dev(torch, Bh)
+    X = torch.zeros_like(B)
+    assert h.solve(B, X, method=method, tol=0.0, maxit=10) == 5
+    hist = h.info()["hist"]
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
+    assert rel(X.cpu().numpy(), ref.X) < X_TOL
+
+
+@pytest.mark.parametrize("method", ["cocg", "cocr"])
+def test_plain_block_methods_full_solve(method):
+    """The plain forms are the less robust ones (Sec. 3: without residual
+    orthonormalization bl_cocg fails on young3c); on this indefinite problem their history
+    amplifies rounding differences faster, so the bounds are 10x the oracle's own response
+    to a 1e-16 relative perturbation of B (history, m <= 20) and twice its iteration-count
+    change plus 5%."""
+    torch = need_gpu()
+    pr = P.helmholtz2d_n1024_p4(method)
+    A = pr.A.to_scipy()
+    f = O.bl_cocg if method == "cocg" else O.bl_cocr
+    ref = f(A, pr.B, tol=1e-10, maxit=pr.maxit)
+    Bp = pr.B * (1.0 + 1e-16 * np.random.default_rng(0).standard_normal(pr.B.shape))
+    refp = f(A, Bp, tol=1e-10, maxit=pr.maxit)
+    m = min(21, len(ref.hist), len(refp.hist))
+    hist_sens = np.max(np.abs(np.array(refp.hist[:m]) - np.array(ref.hist[:m])) / np.array(ref.hist[:m]))
+    h = _handle(pr.A)
+    B = to_dev(torch, pr.B)
+    X = torch.zeros_like(B)
+    st = h.solve(B, X, method=method, tol=1e-10, maxit=pr.maxit)
+    info = h.info()
+    assert st == 0 and ref.status == "converged"
+    assert abs(info["iters"] - ref.iters) <= 2 * abs(refp.iters - ref.iters) + max(3, ref.iters // 20)
+    dev = np.max(np.abs(info["hist"][:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m]))
+    assert dev < max(HIST_TOL, 10 * hist_sens), (dev, hist_sens)
+    assert info["relres_true"] < 1e-8
