@@ -108,6 +108,24 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
                          int maxit);
 
 /*
+ * blcoc_solve_batched - solve nsys independent systems A_i X_i = B_i (one handle each,
+ * p[i] right-hand sides) with the same rq method, tol and maxit.  Every system keeps its
+ * own workspace, control block and p x p factors; one CUDA graph holds all live systems'
+ * next iterations as parallel branches, so one graph launch advances every unconverged
+ * system (converged ones return at once) and small systems share the GPU.
+ * With autotune != 0 the first rounds run under different launch shapes (row-pass grids
+ * sized for all / 1/2 / 1/4 of the SMs, graph batches of 8 / 16 / 32 iterations) and the
+ * fastest per system-iteration is kept; blcoc_last_error(hs[0]) then names it.
+ * B[i], X[i]: device pointers.  ms_per_iter_out (may be NULL): device time per
+ * system-iteration over the whole batch.  Per-system results: blcoc_get_info(hs[i]).
+ * Returns BLCOC_OK if every system converged, else the first non-OK status.
+ * The paper solves one system at a time; batching many is this library's addition.
+ */
+blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
+                                 const int* p, blcoc_method method, double tol, int maxit, int autotune,
+                                 double* ms_per_iter_out);
+
+/*
  * blcoc_get_info - results of the last solve.
  *   iters            : number of iterations taken (the iterate X holds is X_iters).
  *   relres_recursive : ||xi_iters||_F / ||B||_F.

@@ -50,6 +50,8 @@ SIGNATURES = {
                                               C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "blcoc_set_values": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "blcoc_sampled_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "blcoc_solve_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                      C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "blcoc_destroy": (C.c_int, [C.c_void_p]),
     "blcoc_status_string": (C.c_char_p, [C.c_int]),
     "blcoc_last_error": (C.c_char_p, [C.c_void_p]),
@@ -272,6 +274,32 @@ class Handle:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def solve_batched(handles, Bs, Xs, method="cocr_rq", tol=1e-10, maxit=None, autotune=True):
+    """blcoc_solve_batched over lists of Handles and device tensors; returns (status,
+    ms per system-iteration, autotune message)."""
+    lib = load_library()
+    k = len(handles)
+    if not (len(Bs) == len(Xs) == k):
+        raise ValueError("handles, Bs and Xs must have the same length")
+    for h, b, x in zip(handles, Bs, Xs):
+        _check_block(b, h.n, "B")
+        _check_block(x, h.n, "X")
+        if not (_is_cuda(b) and _is_cuda(x)):
+            raise ValueError("batched solves take device tensors")
+    hs = (C.c_void_p * k)(*[h._h.value for h in handles])
+    bp = (C.c_void_p * k)(*[_ptr(b)[0] for b in Bs])
+    xp = (C.c_void_p * k)(*[_ptr(x)[0] for x in Xs])
+    ps = (C.c_int * k)(*[int(b.shape[1]) for b in Bs])
+    maxit = max(h.n for h in handles) if maxit is None else int(maxit)
+    ms = C.c_double()
+    st = lib.blcoc_solve_batched(k, hs, bp, xp, ps, METHODS[method] if isinstance(method, str) else int(method),
+                                 float(tol), maxit, 1 if autotune else 0, C.byref(ms))
+    msg = lib.blcoc_last_error(hs[0]).decode() if k else ""
+    if st not in (BLCOC_OK, BLCOC_NOT_CONVERGED, BLCOC_BREAKDOWN):
+        raise BlcocError(st, msg or lib.blcoc_last_error(None).decode())
+    return st, ms.value, msg
 
 
 # ------------------------------------------------------------------ same names as the ABI

@@ -275,7 +275,7 @@ struct Solver {
     if (in) a.W = in;   // spmm_gram gathers a.W
     a.ne = ne;
     a.flag = flag;
-    a.grid = K->grid(h->n, kind, h->num_sms);
+    a.grid = K->grid(h->n, kind, sms());
     Timer t{kind, batch_iter, nullptr, nullptr};
     if (timers) {
       t.e0 = next_event();
@@ -313,6 +313,8 @@ struct Solver {
     ++launches;
   }
   int plain = 0;   // 1: plain block method (Algorithm 1 / derived block COCG)
+  int grid_sms = 0;   // SMs the row passes size their grid for (0 = all)
+  int sms() const { return grid_sms > 0 ? grid_sms : h->num_sms; }
   void small(SmallKind k, int ne) {
     Timer t;
     timed_begin(t, kKindSmall0 + (int)k);
@@ -363,7 +365,7 @@ struct Solver {
         a.V = a.U;                                       // U_{m+1} = A S_{m+1}
         a.ne = E;
         a.flag = 4;                                      // gram U^T U
-        a.grid = K->grid(h->n, K_SPMM_GRAM, h->num_sms);
+        a.grid = K->grid(h->n, K_SPMM_GRAM, sms());
         Timer t;
         timed_begin(t, K_SPMM_GRAM);
         K->spmm_gram(a, h->s);
@@ -972,6 +974,201 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
     }
     default: h->err = "solve ended in an unknown state"; return BLCOC_ERR_CUDA;
   }
+}
+
+blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
+                                 const int* p, blcoc_method method, double tol, int maxit, int autotune,
+                                 double* ms_per_iter_out) {
+  if (nsys < 1 || !hs || !B || !X || !p) return invalid(nullptr, "blcoc_solve_batched: NULL argument or nsys < 1");
+  if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ) return invalid(nullptr, "batched: rq methods only");
+  if (!(tol >= 0.0) || std::isinf(tol) || maxit < 0) return invalid(nullptr, "batched: bad tol or maxit");
+  const int dev = hs[0]->dev;
+  for (int i = 0; i < nsys; ++i) {
+    if (!hs[i] || hs[i]->dev != dev) return invalid(nullptr, "batched: handles must be non-NULL and on one device");
+    if (p[i] < 1 || p[i] > BLCOC_MAX_P) return invalid(nullptr, "batched: p must be in [1, 32]");
+    if (!B[i] || !X[i] || B[i] == X[i]) return invalid(nullptr, "batched: B[i], X[i] must be distinct device pointers");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return invalid(nullptr, "batched: each system needs its own handle");
+  }
+  blcoc_ctx* h0 = hs[0];
+  CK(h0, cudaSetDevice(dev));
+  std::vector<Solver> sv;
+  sv.reserve(nsys);
+  std::vector<char> live(nsys, 0);
+  for (int i = 0; i < nsys; ++i) {
+    blcoc_ctx* h = hs[i];
+    h->err.clear();
+    blcoc_status st = ensure_ws(h, p[i]);
+    if (st != BLCOC_OK) return st;
+    if (h->hist_cap < maxit + 1) {
+      if (h->hist) cudaFree(h->hist);
+      h->hist = nullptr;
+      h->hist_cap = 0;
+      CK(h, cudaMalloc(&h->hist, (size_t)(maxit + 1) * sizeof(double)));
+      h->hist_cap = maxit + 1;
+    }
+    CK(h, cudaEventRecord(h->ev, h->user_stream));
+    CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
+    int PP = 0;
+    sv.push_back(Solver{h, kernels_for(p[i], &PP), PP, p[i], (int)method, (const double2*)B[i], (double2*)X[i]});
+    sv.back().K->prepare();
+    sv.back().use_fp64_blocks();
+    Ctrl c0{};
+    c0.maxit = maxit;
+    c0.tol = tol;
+    CK(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->s));
+    sv.back().setup_residual();
+    CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+  }
+  for (int i = 0; i < nsys; ++i) {
+    blcoc_ctx* h = hs[i];
+    CK(h, cudaStreamSynchronize(h->s));
+    if (h->h_ctrl->done == 1 && h->h_ctrl->sumsq_b == 0.0) {
+      CK(h, cudaMemsetAsync(X[i], 0, (size_t)h->n * p[i] * sizeof(double2), h->s));
+    } else if (!h->h_ctrl->done) {
+      sv[i].setup_rest();
+      live[i] = 1;
+    }
+    CK(h, cudaGetLastError());
+  }
+  cudaStream_t main_s = nullptr;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join(nsys, nullptr);
+  CK(h0, cudaStreamCreateWithFlags(&main_s, cudaStreamNonBlocking));
+  CK(h0, cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+  for (auto& e : join) CK(h0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t t0, t1;
+  CK(h0, cudaEventCreate(&t0));
+  CK(h0, cudaEventCreate(&t1));
+  for (int i = 0; i < nsys; ++i) {   // the batch stream starts after every setup
+    CK(h0, cudaEventRecord(join[i], hs[i]->s));
+    CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
+  }
+  // one graph: every live system's `poll` iterations as a parallel branch
+  auto capture = [&](int poll, int grid_sms, cudaGraphExec_t* exec, int* nlaunch) -> blcoc_status {
+    cudaGraph_t graph = nullptr;
+    CK(h0, cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
+    CK(h0, cudaEventRecord(fork_ev, main_s));
+    int launches = 0;
+    for (int i = 0; i < nsys; ++i) {
+      if (!live[i]) continue;
+      CK(h0, cudaStreamWaitEvent(hs[i]->s, fork_ev, 0));
+      sv[i].grid_sms = grid_sms;
+      const int before = sv[i].launches;
+      for (int k = 0; k < poll; ++k) sv[i].iteration();
+      launches += sv[i].launches - before;
+      sv[i].launches = before;
+      CK(h0, cudaEventRecord(join[i], hs[i]->s));
+      CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
+    }
+    cudaError_t e = cudaStreamEndCapture(main_s, &graph);
+    if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaStreamEndCapture");
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaGraphInstantiate");
+    *nlaunch = launches;
+    return BLCOC_OK;
+  };
+  // candidate launch shapes: grid sized for all / half / a quarter of the SMs (several
+  // systems then share the GPU), graph batches of 8, 16 or 32 iterations
+  struct Shape { int poll, grid_sms; };
+  std::vector<Shape> cand = {{16, h0->num_sms}};
+  if (autotune) cand = {{16, h0->num_sms}, {16, h0->num_sms / 2}, {16, h0->num_sms / 4}, {8, h0->num_sms / 2},
+                        {32, h0->num_sms / 2}};
+  size_t ci = 0;
+  int best = -1, cur = -1;
+  double best_ms = 1e300;
+  cudaGraphExec_t exec = nullptr;
+  int exec_launches = 0, exec_poll = 0;
+  double total_ms = 0.0;
+  int64_t total_iters = 0;
+  int64_t launches = 0;
+  blcoc_status st = BLCOC_OK;
+  for (int round = 0;; ++round) {
+    bool any = false;
+    for (int i = 0; i < nsys; ++i) any = any || live[i];
+    if (!any) break;
+    const int idx = (ci < cand.size()) ? (int)ci : best;
+    const Shape sh = cand[idx];
+    if (!exec || idx != cur) {   // (re)capture only when the launch shape changes
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      st = capture(sh.poll, sh.grid_sms, &exec, &exec_launches);
+      if (st != BLCOC_OK) break;
+      exec_poll = sh.poll;
+      cur = idx;
+    }
+    std::vector<int> it_before(nsys);
+    for (int i = 0; i < nsys; ++i) it_before[i] = hs[i]->h_ctrl->iter;
+    CK(h0, cudaEventRecord(t0, main_s));
+    CK(h0, cudaGraphLaunch(exec, main_s));
+    CK(h0, cudaEventRecord(t1, main_s));
+    launches += exec_launches;
+    for (int i = 0; i < nsys; ++i)
+      if (live[i]) CK(h0, cudaMemcpyAsync(hs[i]->h_ctrl, hs[i]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, main_s));
+    CK(h0, cudaStreamSynchronize(main_s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t0, t1);
+    int64_t its = 0;
+    for (int i = 0; i < nsys; ++i)
+      if (live[i]) {
+        its += hs[i]->h_ctrl->iter - it_before[i];
+        if (hs[i]->h_ctrl->done) live[i] = 0;
+        if (round > (maxit + exec_poll) / (exec_poll > 0 ? exec_poll : 1) + 8) {
+          h0->err = "batched: iteration control did not stop";
+          st = BLCOC_ERR_CUDA;
+        }
+      }
+    total_ms += ms;
+    total_iters += its;
+    if (ci < cand.size()) {   // autotuning round: time per system-iteration
+      const double per = its > 0 ? ms / (double)its : 1e300;
+      if (per < best_ms) {
+        best_ms = per;
+        best = (int)ci;
+      }
+      ++ci;
+    }
+    if (st != BLCOC_OK) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (ms_per_iter_out) *ms_per_iter_out = total_iters > 0 ? total_ms / (double)total_iters : 0.0;
+  // finish every system like a single solve: true residual, history, status
+  blcoc_status worst = st;
+  for (int i = 0; i < nsys && st == BLCOC_OK; ++i) {
+    blcoc_ctx* h = hs[i];
+    Solver& s1 = sv[i];
+    s1.grid_sms = 0;
+    s1.true_residual();
+    CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
+    CK(h, cudaStreamSynchronize(h->s));
+    const Ctrl c = *h->h_ctrl;
+    h->iters = c.iter;
+    const double nb = std::sqrt(c.sumsq_b);
+    h->trr = nb > 0 ? c.trr / nb : 0.0;
+    h->hist_h.assign(c.nhist, 0.0);
+    if (c.nhist > 0)
+      CK(h, cudaMemcpy(h->hist_h.data(), h->hist, (size_t)c.nhist * sizeof(double), cudaMemcpyDeviceToHost));
+    h->relres = c.done == 3 ? (c.nhist > 0 ? h->hist_h[c.nhist - 1] : h->trr) : c.relres;
+    h->xi_h.assign(2 * p[i] * p[i], 0.0);
+    CK(h, cudaEventRecord(h->ev, h->s));
+    CK(h, cudaStreamWaitEvent(h->user_stream, h->ev, 0));
+    h->stat_launches = launches;
+    blcoc_status si = c.done == 1 || nb == 0 ? BLCOC_OK : (c.done == 2 ? BLCOC_NOT_CONVERGED : BLCOC_BREAKDOWN);
+    if (si != BLCOC_OK && worst == BLCOC_OK) worst = si;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  for (auto& e : join) cudaEventDestroy(e);
+  cudaEventDestroy(fork_ev);
+  cudaStreamDestroy(main_s);
+  if (best >= 0 && h0) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "autotuned launch shape: graph batch %d iterations, grid for %d SMs",
+             cand[best].poll, cand[best].grid_sms);
+    if (worst == BLCOC_OK) h0->err = buf;
+  }
+  return worst;
 }
 
 blcoc_status blcoc_get_info(blcoc_handle h, int* iters, double* relres_recursive, double* relres_true, double* hist,

@@ -223,3 +223,22 @@ def helmholtz3d_n2097152_p32(method: str = "cocr_rq", maxit: int = 50000) -> Pro
     N = 128
     return Problem("helmholtz3d_128cube_k40_p32", helmholtz_3d_absorbing(N, 40.0), complex_normal(N**3, 32, 1),
                    method, 1e-10, maxit)
+
+
+def helmholtz2d_batch(count: int = 64, seed: int = 3, side_range=(64, 512), k_range=(5.0, 30.0),
+                      damping_range=(0.02, 0.1), p_choices=(1, 2, 4, 8, 16)):
+    """Independent 2D 5-point Helmholtz systems of uneven size: for each system, from one
+    ``default_rng(seed)`` stream in this order, grid side ~ U{side_range}, k ~ U[k_range],
+    damping ~ U[damping_range], p ~ choice(p_choices); then B is complex normal with seed
+    ``1000 * seed + i``."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        side = int(rng.integers(side_range[0], side_range[1] + 1))
+        k = float(rng.uniform(*k_range))
+        damping = float(rng.uniform(*damping_range))
+        p = int(rng.choice(p_choices))
+        A = helmholtz_2d(side, k, damping)
+        out.append(Problem(f"helmholtz2d_{side}x{side}_k{k:.1f}_p{p}", A, complex_normal(A.n, p, 1000 * seed + i),
+                           "cocr_rq", 1e-10, 20000, extra={"side": side, "k": k, "damping": damping}))
+    return out

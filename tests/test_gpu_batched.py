@@ -1,0 +1,80 @@
+"""Batched solves (blcoc_solve_batched): many independent systems of uneven n and p.
+
+* without autotuning the launch shape equals the single solve's, so every system's
+  iterate, iteration count and history must equal a separate blcoc_solve bit for bit;
+* with autotuning (grids sized for fewer SMs: the cross-CTA reduction order changes)
+  every system must still converge to the tolerance with the oracle-parity history
+  bound (1e-8 for m <= 20) against its separate solve.
+"""
+import numpy as np
+import pytest
+
+from paper_1601_05362_gb300 import problems as P
+from gpu_common import need_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(torch, count=10):
+    from paper_1601_05362_gb300 import blcoc
+    probs = P.helmholtz2d_batch(count, seed=5, side_range=(20, 72), k_range=(3.0, 9.0))
+    hs = [blcoc.Handle.from_csr(pr.A) for pr in probs]
+    Bs = [to_dev(torch, pr.B) for pr in probs]
+    return probs, hs, Bs
+
+
+def _separate(torch, hs, Bs):
+    out = []
+    for h, B in zip(hs, Bs):
+        X = torch.zeros_like(B)
+        assert h.solve(B, X, tol=1e-10, maxit=5000) == 0
+        out.append((X.cpu().numpy(), h.info()))
+    return out
+
+
+def test_batched_equals_separate_solves_bitwise():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    probs, hs, Bs = _batch(torch)
+    ref = _separate(torch, hs, Bs)
+    Xs = [torch.zeros_like(B) for B in Bs]
+    st, ms, msg = blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False)
+    assert st == blcoc.BLCOC_OK
+    assert ms > 0
+    for (Xr, ir), X, h in zip(ref, Xs, hs):
+        info = h.info()
+        assert info["iters"] == ir["iters"]
+        assert np.array_equal(X.cpu().numpy(), Xr)
+        assert np.array_equal(info["hist"], ir["hist"])
+    for h in hs:
+        h.close()
+
+
+def test_batched_autotuned_converges():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    probs, hs, Bs = _batch(torch, 12)
+    ref = _separate(torch, hs, Bs)
+    Xs = [torch.zeros_like(B) for B in Bs]
+    st, ms, msg = blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=True)
+    assert st == blcoc.BLCOC_OK
+    assert msg.startswith("autotuned launch shape")
+    for (Xr, ir), X, h in zip(ref, Xs, hs):
+        info = h.info()
+        assert info["relres_true"] <= 1e-9
+        m = min(21, len(ir["hist"]), len(info["hist"]))
+        assert np.max(np.abs(info["hist"][:m] - ir["hist"][:m]) / ir["hist"][:m]) < 1e-8
+        assert abs(info["iters"] - ir["iters"]) <= max(3, ir["iters"] // 20)
+    for h in hs:
+        h.close()
+
+
+def test_batched_rejects_shared_handles():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    probs, hs, Bs = _batch(torch, 2)
+    Xs = [torch.zeros_like(B) for B in Bs]
+    with pytest.raises(blcoc.BlcocError):
+        blcoc.solve_batched([hs[0], hs[0]], [Bs[0], Bs[0]], Xs[:1] * 2)
+    for h in hs:
+        h.close()
