@@ -189,6 +189,12 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  product per iteration instead of Algorithm 3's recurrence
  *                  U_{m+1} = V_{m+1} + U_m beta'_m (equal in exact arithmetic; the
  *                  recurrence is the default, 0).
+ *   "fp64_tc"    : BLCOC_COCR_RQ with p <= 16: 1 runs the p x p block updates (right-
+ *                  multiplications by alpha', alpha'xi, beta', tau^{-1}) on the bf16 tensor
+ *                  cores by exact integer slicing of both operands (eight 7-bit digits,
+ *                  43 slice products, exact fp32 partial sums), to about FP64 accuracy;
+ *                  the Grams, the sparse product and the p x p stages stay FP64.  0 (default)
+ *                  computes them with FP64 FMAs.
  *   "u_explicit_mixed": the same for the complex64 inner solves of BLCOC_COCR_RQ_MIXED
  *                  (default 1: the recurrence drifts quickly in single precision).
  *   "timing"     : 1 brackets every kernel of the iterations with CUDA events on

@@ -16,6 +16,7 @@
 
 #include "../../include/blcoc.h"
 #include "blcoc_common.cuh"
+#include "blcoc_ozaki.cuh"
 #include "blcoc_small.h"
 
 using namespace blcoc;
@@ -111,6 +112,8 @@ struct blcoc_ctx {
   int inner_maxit = 0;        // mixed precision: per inner solve (0 = remaining budget)
   int outer_maxit = 40;
   int outer_iters = 0;
+  int fp64_tc = 0;            // cocr, p <= 16: p x p applies on the tensor cores by exact slicing
+  uint2* ozbuf = nullptr;     // their factor fragments
   int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
   int u_explicit_mixed = 1;   // the same for the complex64 inner solves
   Graph graph;
@@ -252,6 +255,7 @@ struct Solver {
     a.mats = h->mats;
     a.partials = h->partials;
     a.ctrl = h->ctrl;
+    a.oz = oz;
     return a;
   }
   int launches = 0;
@@ -313,12 +317,13 @@ struct Solver {
     ++launches;
   }
   int plain = 0;   // 1: plain block method (Algorithm 1 / derived block COCG)
+  uint2* oz = nullptr;   // factor fragments when the applies run on the tensor cores
   int grid_sms = 0;   // SMs the row passes size their grid for (0 = all)
   int sms() const { return grid_sms > 0 ? grid_sms : h->num_sms; }
   void small(SmallKind k, int ne) {
     Timer t;
     timed_begin(t, kKindSmall0 + (int)k);
-    launch_small(k, p, method + 16 * plain, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s);
+    launch_small(k, p, method + 16 * plain, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s, oz);
     timed_end(t);
     ++launches;
   }
@@ -449,6 +454,7 @@ blcoc_status blcoc_destroy(blcoc_handle h) {
   free_ws(h);
   free_ws32(h);
   if (h->vaf) cudaFree(h->vaf);
+  if (h->ozbuf) cudaFree(h->ozbuf);
   if (h->Bst) cudaFree(h->Bst);
   if (h->Xst) cudaFree(h->Xst);
   if (h->rp) cudaFree(h->rp);
@@ -604,6 +610,12 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     if (value < 1 || value > 4096) return invalid(h, "poll must be in [1, 4096]");
     if (h->poll != (int)value) h->graph.reset();
     h->poll = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "fp64_tc")) {
+    if (value != 0 && value != 1) return invalid(h, "fp64_tc must be 0 or 1");
+    h->graph.reset();
+    h->fp64_tc = (int)value;
     return BLCOC_OK;
   }
   if (!strcmp(key, "u_explicit") || !strcmp(key, "u_explicit_mixed")) {
@@ -918,6 +930,12 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   const int base_method = plain ? (method == BLCOC_COCR ? BLCOC_COCR_RQ : BLCOC_COCG_RQ) : (int)method;
   int PP = 0;
   Solver sv{h, kernels_for(p, &PP), PP, p, base_method, dB, dX};
+  const bool tc = h->fp64_tc && !plain && base_method == BLCOC_COCR_RQ && (PP == 8 || PP == 16);
+  if (tc) {
+    if (!h->ozbuf) CK(h, cudaMalloc(&h->ozbuf, (size_t)OZ_NSLOTS * OZ_SLOT_U2 * sizeof(uint2)));
+    sv.K = PP == 8 ? &kernel_set_tc<8>() : &kernel_set_tc<16>();
+    sv.oz = h->ozbuf;
+  }
   sv.K->prepare();
   sv.use_fp64_blocks();
   sv.plain = plain ? 1 : 0;
@@ -937,7 +955,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   } else if (!h->h_ctrl->done) {
     sv.setup_rest();
     CK(h, cudaGetLastError());
-    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain, maxit);
+    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0), maxit);
     if (st != BLCOC_OK) return st;
   }
   // true residual of the returned iterate

@@ -127,6 +127,7 @@ struct PassArgs {
   const double2* B;
   const double2* mats;
   double2* partials;  // [grid][ne]
+  const uint2* oz;    // exact-slice fragments of the p x p factors (tensor-core applies)
   int ne;             // partial entries per CTA
   Ctrl* ctrl;
   int flag;           // kernel-specific switch (first pass / apply T / norm only / cocg grams)
@@ -153,6 +154,8 @@ struct KernelSet {
 // of the mixed-precision refinement (the residual pass stays FP64 and writes its R in
 // complex64, the Grams are summed in FP64, the p x p stages are the FP64 kernels).
 template <int PP, typename S = double> const KernelSet& kernel_set();
+// FP64 path whose p x p applies run on the bf16 tensor cores by exact slicing (PP 8, 16)
+template <int PP> const KernelSet& kernel_set_tc();
 
 // Sets the message blcoc_last_error(NULL) returns (calling thread only).
 void set_global_error(const char* msg);

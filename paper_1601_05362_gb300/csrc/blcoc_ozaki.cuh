@@ -1,0 +1,243 @@
+// FP64-accurate products Y (32 rows x p) = X (32 x p) * M (p x p), complex, on the bf16
+// tensor cores (warp-level mma.sync), by exact integer slicing (the scheme of Ozaki,
+// Ogita, Oishi and Rump: split both operands into slices whose pairwise products are
+// exact in the accumulator, multiply slice by slice, add the exact partial products).
+//
+// Complex as real: Y' = [Yr | Yi] = [Xr | Xi] * [[Mr, Mi], [-Mi, Mr]] with K = N = 2p.
+// Slicing: every row of X' is scaled by 2^e (e: above its largest magnitude) and every
+// column of M' by 2^f; each value becomes a 56-bit fixed-point magnitude cut into eight
+// 7-bit digits (sign kept), digit s weighted 2^(e - 7 s).  A digit (<= 127) is exact in
+// bf16, a digit product (< 2^14) is exact in fp32, and a level L = s + t sums at most 8
+// slice pairs over K <= 32 terms: < 2^23, still exact in the fp32 accumulator.  Levels
+// 2..10 are kept (43 slice products); the dropped levels and the 56-bit cut contribute
+// about 2^-54 of |X'| |M'|, the size of FP64's own rounding in a K-term dot product.
+// Recombination: the nine exact level sums are combined as two 64-bit integers and turned
+// into a double with two conversions and two FMAs, added to the base value.
+//
+// The p x p stage kernels write each factor already split, in the B-fragment order of
+// mma.m16n8k16 (`oz_emit_factor`); the row passes split X' in registers (`oz_apply`).
+#pragma once
+
+#include "blcoc_common.cuh"
+
+namespace blcoc {
+
+// per-factor slot in the handle's slice buffer: fragments of the largest supported width
+// (p <= 16) followed by the 2p column exponents
+constexpr int OZ_SLOT_U2 = 8 * 2 * 4 * 32 + 32;   // uint2 units (16 KB + 256 B)
+enum OzSlot { OZ_T = 0, OZ_ALPHA, OZ_ALPHAXI, OZ_BETA, OZ_NSLOTS };
+__host__ __device__ inline const int* oz_colexp_of(const uint2* slot) {
+  return reinterpret_cast<const int*>(slot + 8 * 2 * 4 * 32);
+}
+__host__ __device__ inline int* oz_colexp_of(uint2* slot) { return reinterpret_cast<int*>(slot + 8 * 2 * 4 * 32); }
+
+constexpr int OZ_NSL = 8;    // digits per value
+constexpr int OZ_DB = 7;     // bits per digit
+constexpr int OZ_LMAX = 10;  // highest level kept (s + t)
+constexpr int OZ_NLEV = OZ_LMAX - 1;   // levels 2..10
+
+template <int PP>
+struct OzGeo {
+  static constexpr int NR = 2 * PP;        // real width
+  static constexpr int KS = NR / 16;       // k16 steps
+  static constexpr int NT = NR / 8;        // n8 tiles
+  static constexpr int FRAG = OZ_NSL * KS * NT * 32;   // uint2 per factor
+};
+
+// biased exponent field of |x| (0 for zero and subnormals, 2047 for inf/nan)
+__device__ __forceinline__ int oz_bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// 56-bit fixed-point magnitude of x relative to a row/column whose largest biased
+// exponent is eb (|x| < 2^(eb - 1022)): F = |x| 2^(56 - (eb - 1022)), truncated.
+__device__ __forceinline__ unsigned long long oz_fixed(double x, int eb) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ev = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0x000FFFFFFFFFFFFFull;
+  int e = ev;
+  if (ev == 0) e = 1;                      // subnormal: no implicit bit
+  else m |= 0x0010000000000000ull;         // implicit bit
+  const int sh = max(eb, 1) - e;           // >= 0 (subnormals count as exponent 1)
+  if (m == 0 || sh >= 59) return 0ull;
+  return (m << 3) >> sh;
+}
+
+// bf16 bit pattern of the signed digit (sign bit | magnitude d <= 127), exact:
+// float(d) through the 2^23 magic constant, top half of the float.
+__device__ __forceinline__ unsigned oz_bf16(unsigned d, unsigned sign) {
+  const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+  return (__float_as_uint(f) >> 16) | (sign << 15);
+}
+
+// Real entry (k, j) of M' = [[Mr, Mi], [-Mi, Mr]] for a p x p complex M (row stride ld),
+// zero outside p in either half.
+template <int PP>
+__device__ __forceinline__ double oz_mbig(const double2* M, int ld, int p, int k, int j) {
+  const int kk = k % PP, jj = j % PP;
+  if (kk >= p || jj >= p) return 0.0;
+  const double2 v = M[kk * ld + jj];
+  const bool kim = k >= PP, jim = j >= PP;
+  if (!kim && !jim) return v.x;
+  if (!kim && jim) return v.y;
+  if (kim && !jim) return -v.y;
+  return v.x;
+}
+
+// Split a p x p factor into OZ_NSL bf16 slices in the B-fragment order of mma.m16n8k16
+// (row.col): frag[((t*KS + ks)*NT + nt)*32 + lane] = {rows 16ks+2q, +1 ; rows +8, +9} of
+// column 8nt + g, g = lane/4, q = lane%4.  colexp[j]: largest biased exponent in column j
+// of M'.  All threads of the CTA call this; it synchronises internally.
+template <int PP>
+__device__ void oz_emit_factor(const double2* M, int ld, int p, uint2* __restrict__ frag, int* __restrict__ colexp,
+                               int* sh_colexp) {
+  using G = OzGeo<PP>;
+  for (int j = threadIdx.x; j < G::NR; j += blockDim.x) {
+    int eb = 0;
+    for (int k = 0; k < G::NR; ++k) eb = max(eb, oz_bexp(oz_mbig<PP>(M, ld, p, k, j)));
+    sh_colexp[j] = eb;
+    colexp[j] = eb;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < G::KS * G::NT * 32; w += blockDim.x) {
+    const int lane = w & 31, nt = (w >> 5) % G::NT, ks = (w >> 5) / G::NT;
+    const int g = lane >> 2, q = lane & 3, j = 8 * nt + g;
+    const int eb = sh_colexp[j];
+    unsigned long long F[4];
+    unsigned sg[4];
+    const int rows[4] = {16 * ks + 2 * q, 16 * ks + 2 * q + 1, 16 * ks + 2 * q + 8, 16 * ks + 2 * q + 9};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const double v = oz_mbig<PP>(M, ld, p, rows[r], j);
+      F[r] = oz_fixed(v, eb);
+      sg[r] = (__double_as_longlong(v) < 0) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int t = 1; t <= OZ_NSL; ++t) {
+      const int shft = 56 - OZ_DB * t;
+      unsigned h[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) h[r] = oz_bf16((unsigned)((F[r] >> shft) & 127ull), sg[r]);
+      frag[((t - 1) * G::KS + ks) * G::NT * 32 + nt * 32 + lane] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void oz_mma(float (&c)[4], const unsigned (&a)[4], uint2 b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// out = base (+/-) in * M for the warp's 32-row chunk (swizzled [k][32] tiles of double2,
+// columns >= p of `in` are ignored).  `out` may alias `base` or, without a base, `in`.
+// frag / colexp: the factor as written by oz_emit_factor (global memory).
+template <int PP, bool SUB, bool BASE>
+__device__ __forceinline__ void oz_apply(double2* out, const double2* base, const double2* in,
+                                         const uint2* __restrict__ frag, const int* __restrict__ colexp, int p,
+                                         int lane) {
+  using G = OzGeo<PP>;
+  static_assert(PP == 8 || PP == 16, "exact-slice products are built for p <= 16");
+  auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
+  // row exponents (lane = row)
+  int eb_row = 0;
+  for (int k = 0; k < p; ++k) {
+    const double2 v = in[tx(k, lane)];
+    eb_row = max(eb_row, max(oz_bexp(v.x), oz_bexp(v.y)));
+  }
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) {
+    const int ra = 16 * mt + g, rb = ra + 8;
+    const int eba = __shfl_sync(0xffffffffu, eb_row, ra), ebb = __shfl_sync(0xffffffffu, eb_row, rb);
+    // A fragments of all slices: a[t][ks][4]
+    unsigned A[OZ_NSL][G::KS][4];
+#pragma unroll
+    for (int ks = 0; ks < G::KS; ++ks) {
+      // real columns 16ks + {2q, 2q+1, 2q+8, 2q+9}; rows ra, rb
+      unsigned long long F[8];
+      unsigned sg[8];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int col = 16 * ks + 2 * q + (c & 1) + 8 * (c >> 1);
+        const int kc = col % PP;
+        const bool im = col >= PP;
+        double va = 0.0, vb = 0.0;
+        if (kc < p) {
+          const double2 xa = in[tx(kc, ra)], xb = in[tx(kc, rb)];
+          va = im ? xa.y : xa.x;
+          vb = im ? xb.y : xb.x;
+        }
+        F[2 * c] = oz_fixed(va, eba);
+        sg[2 * c] = (__double_as_longlong(va) < 0) ? 1u : 0u;
+        F[2 * c + 1] = oz_fixed(vb, ebb);
+        sg[2 * c + 1] = (__double_as_longlong(vb) < 0) ? 1u : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < OZ_NSL; ++t) {
+        const int shft = 56 - OZ_DB * (t + 1);
+        unsigned h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) h[e] = oz_bf16((unsigned)((F[e] >> shft) & 127ull), sg[e]);
+        // a0,a1: (ra, 2q,2q+1)  a2,a3: (rb, 2q,2q+1)  a4,a5: (ra, 2q+8,+9)  a6,a7: (rb, 2q+8,+9)
+        A[t][ks][0] = h[0] | (h[2] << 16);
+        A[t][ks][1] = h[1] | (h[3] << 16);
+        A[t][ks][2] = h[4] | (h[6] << 16);
+        A[t][ks][3] = h[5] | (h[7] << 16);
+      }
+    }
+#pragma unroll 1
+    for (int nt = 0; nt < G::NT; ++nt) {
+      uint2 Bf[OZ_NSL][G::KS];
+#pragma unroll
+      for (int t = 0; t < OZ_NSL; ++t)
+#pragma unroll
+        for (int ks = 0; ks < G::KS; ++ks) Bf[t][ks] = __ldg(frag + (t * G::KS + ks) * G::NT * 32 + nt * 32 + lane);
+      float acc[OZ_NLEV][4];
+#pragma unroll
+      for (int l = 0; l < OZ_NLEV; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.f;
+#pragma unroll
+      for (int s = 1; s <= OZ_NSL; ++s) {
+#pragma unroll
+        for (int t = 1; t <= OZ_NSL; ++t) {
+          if (s + t > OZ_LMAX) continue;
+#pragma unroll
+          for (int ks = 0; ks < G::KS; ++ks) oz_mma(acc[s + t - 2], A[s - 1][ks], Bf[t - 1][ks]);
+        }
+      }
+      // recombination of the four outputs held by this lane:
+      // (ra, 8nt+2q), (ra, 8nt+2q+1), (rb, 8nt+2q), (rb, 8nt+2q+1)
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        long long hi = 0, lo = 0;
+#pragma unroll
+        for (int L = 2; L <= 6; ++L) hi += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (6 - L));
+#pragma unroll
+        for (int L = 7; L <= OZ_LMAX; ++L) lo += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (10 - L));
+        const int row = (o < 2) ? ra : rb;
+        const int col = 8 * nt + 2 * q + (o & 1);
+        const int ebr = (o < 2) ? eba : ebb;
+        const int ebc = __ldg(colexp + col);
+        // value = (hi 2^-42 + lo 2^-70) 2^(e_r + f_c), e = eb - 1022
+        const int sc = (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022) - 42;
+        double v = fma((double)lo, 0x1p-28, (double)hi);
+        if (ebr == 2047 || ebc == 2047) v = __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
+        else if (sc >= -1020 && sc <= 1020) v *= __longlong_as_double((long long)(sc + 1023) << 52);
+        else v = ldexp(v, sc);
+        const int kc = col % PP;
+        if (kc < p) {
+          double2 cur = BASE ? base[tx(kc, row)] : make_double2(0.0, 0.0);
+          double& dst = (col >= PP) ? cur.y : cur.x;
+          dst = SUB ? dst - v : dst + v;
+          // the real and imaginary halves of one complex output are written by different
+          // lanes (n-tiles nt and nt + NT/2): write only this lane's half
+          if (col >= PP) out[tx(kc, row)].y = cur.y;
+          else out[tx(kc, row)].x = cur.x;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace blcoc

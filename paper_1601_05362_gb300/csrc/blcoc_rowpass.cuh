@@ -21,6 +21,7 @@
 #pragma once
 
 #include "blcoc_common.cuh"
+#include "blcoc_ozaki.cuh"
 
 namespace blcoc {
 
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
 // out = Y T (flag=1, cocr: V = A Q = (A W) tau^{-1}) or out = Y (flag=0, cocg: a.W = S,
 // out = A S).  flag&F_UEXPL: gram Y^T Y instead (explicit U = A S and U^T U).
 // Partials: [W^T Y or Y^T Y tri].
-template <int PP, typename S>
+template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
@@ -437,7 +438,12 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
     __syncwarp();
     g.template add<false>((a.flag & F_UEXPL) ? tY : tW, tY, lane);
     if (applyT) {
-      tri_apply_inplace<PP, S>(tY, T, p, lane);
+      if constexpr (OZ) {
+        const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
+        oz_apply<PP, false, false>(tY, nullptr, tY, fz, oz_colexp_of(fz), p, lane);
+      } else {
+        tri_apply_inplace<PP, S>(tY, T, p, lane);
+      }
       __syncwarp();
     }
     store_tile<PP>(blk<C>(a.V), tY, r0, n, p, lane);
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
 
 // bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): W_{m+1} = Q_m - U_m alpha'_m
 // (Q_m stored by the previous pass C); gram W^H W for the Cholesky QR.
-template <int PP, typename S>
+template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
@@ -487,7 +493,12 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
     load_tile<PP>(tW, blk<C>(a.Q), r0, n, p, lane);
     load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
-    apply_full<PP, S, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
+    if constexpr (OZ) {
+      const uint2* fz = a.oz + OZ_ALPHA * OZ_SLOT_U2;
+      oz_apply<PP, true, true>(tW, tW, tU, fz, oz_colexp_of(fz), p, lane);
+    } else {
+      apply_full<PP, S, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
+    }
     __syncwarp();
     g.template add<true>(tW, tW, lane);
     store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
@@ -503,7 +514,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
 //   U_{m+1} = V_{m+1} + U_m beta'_m;  gram U^T U (next alpha').
 // flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.  flag&F_UEXPL: no U update
 // and no gram (U_{m+1} = A S_{m+1} is formed by the SpMM that follows).
-template <int PP, typename S>
+template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
@@ -536,15 +547,30 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
       load_tile<PP>(b2, blk<C>(a.X), r0, n, p, lane);
     }
     __syncwarp();
-    tri_apply_inplace<PP, S>(b0, T, p, lane);             // Q_{m+1}
+    if constexpr (OZ) {
+      const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
+      oz_apply<PP, false, false>(b0, nullptr, b0, fz, oz_colexp_of(fz), p, lane);
+    } else {
+      tri_apply_inplace<PP, S>(b0, T, p, lane);             // Q_{m+1}
+    }
     __syncwarp();
     store_tile<PP>(blk<C>(a.Q), b0, r0, n, p, lane);
     if (!first) {
-      apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
+      if constexpr (OZ) {
+        const uint2* fz = a.oz + OZ_ALPHAXI * OZ_SLOT_U2;
+        oz_apply<PP, false, true>(b2, b2, b1, fz, oz_colexp_of(fz), p, lane);
+      } else {
+        apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
+      }
       __syncwarp();
       store_tile<PP>(blk<C>(a.X), b2, r0, n, p, lane);
       __syncwarp();
-      apply_full<PP, S, false>(b2, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
+      if constexpr (OZ) {
+        const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
+        oz_apply<PP, false, true>(b2, b0, b1, fz, oz_colexp_of(fz), p, lane);
+      } else {
+        apply_full<PP, S, false>(b2, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
+      }
       __syncwarp();
       store_tile<PP>(blk<C>(a.S), b2, r0, n, p, lane);
     } else {
@@ -557,7 +583,12 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
     if (!first) load_tile<PP>(b2, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
     if (!first) {
-      apply_full<PP, S, false>(b1, b1, b2, BE, p, lane);  // U_{m+1} = V + U beta'
+      if constexpr (OZ) {
+        const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
+        oz_apply<PP, false, true>(b1, b1, b2, fz, oz_colexp_of(fz), p, lane);
+      } else {
+        apply_full<PP, S, false>(b1, b1, b2, BE, p, lane);  // U_{m+1} = V + U beta'
+      }
       __syncwarp();
     }
     g.template add<false>(b1, b1, lane);
@@ -746,6 +777,39 @@ const KernelSet& kernel_set() {
       &launch_pass<PP, S, K_AXPY, k_axpy<PP, S>>,
       &pass_grid<PP, S>,
       &prepare_pass_kernels<PP, S>,
+  };
+  return ks;
+}
+
+template <int PP>
+void prepare_pass_kernels_tc() {
+  prepare_pass_kernels<PP, double>();
+  static bool done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaFuncSetAttribute(k_spmm_gram<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double>(K_SPMM_GRAM));
+  cudaFuncSetAttribute(k_cocr_passA<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double>(K_COCR_A));
+  cudaFuncSetAttribute(k_cocr_passC<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double>(K_COCR_C));
+  done[dev] = true;
+}
+
+template <int PP>
+const KernelSet& kernel_set_tc() {
+  static const KernelSet ks = {
+      &launch_pass<PP, double, K_RESID, k_resid<PP, double>>,
+      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>>,
+      &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
+      &launch_pass<PP, double, K_COCR_A, k_cocr_passA<PP, double, true>>,
+      &launch_pass<PP, double, K_COCR_C, k_cocr_passC<PP, double, true>>,
+      &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
+      &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
+      &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
+      &pass_grid<PP, double>,
+      &prepare_pass_kernels_tc<PP>,
   };
   return ks;
 }

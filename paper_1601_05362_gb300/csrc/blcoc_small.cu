@@ -7,6 +7,7 @@
 // block is a Cholesky QR: tau^H tau = W^H W with tau upper triangular and a real
 // positive diagonal, T = tau^{-1}.
 #include "blcoc_common.cuh"
+#include "blcoc_ozaki.cuh"
 #include "blcoc_small.h"
 
 namespace blcoc {
@@ -299,8 +300,17 @@ struct SmallShared {
   double gs[2 * (2 * PMAX * (PMAX + 1) / 2 + 2)];
   double red[2 * PMAX + 8];
   int ish[4];
+  int colexp[64];
   double2 m[6][LD * LD];
 };
+
+// Exact-slice fragments of a p x p factor (smem, stride LD) for the tensor-core applies.
+__device__ void emit_oz(uint2* oz, int slot, const double2* M, int p, int* sh) {
+  if (oz == nullptr) return;
+  uint2* f = oz + slot * OZ_SLOT_U2;
+  if (p <= 8) oz_emit_factor<8>(M, LD, p, f, oz_colexp_of(f), sh);
+  else oz_emit_factor<16>(M, LD, p, f, oz_colexp_of(f), sh);
+}
 
 #define SMALL_PROLOGUE                                                  \
   extern __shared__ __align__(16) unsigned char small_raw[];            \
@@ -313,7 +323,7 @@ __device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s
 // inner = 1 (refinement step): the stopping test is relative to ||R_0||_F, the norm of
 // this solve's right-hand side, which is the outer residual.
 __global__ void k_small_setup(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                              int inner, int plain) {
+                              int inner, int plain, uint2* oz) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   sum_stage1(stage1, ncomp, S.gs);
@@ -356,6 +366,7 @@ __global__ void k_small_setup(int p, int method, const double* stage1, int ncomp
   tri_inv_upper(S.m[1], S.m[2], p, S.red);
   gstore(slot(mats, M_XI), S.m[1], p);
   gstore(slot(mats, M_TINV), S.m[2], p);
+  emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     expand_tri(S.gs + 2 * E, S.m[3], p, false);
     matmul(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
@@ -381,7 +392,7 @@ __global__ void k_small_cocr_H0(int p, const double* stage1, int ncomp, double2*
 // (cocg) and RHS = Q^T V (cocr) or Q^T Q (cocg); also alpha'_m xi_m.
 // plain: the stopping test uses ||R_m||_F (Algorithm 1) recorded by the previous stage.
 __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, double* hist,
-                              int plain) {
+                              int plain, uint2* oz) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   const int m = ctrl->iter;
@@ -414,6 +425,8 @@ __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* m
   gstore(slot(mats, M_ALPHA), S.m[2], p);
   matmul(S.m[3], S.m[2], false, S.m[0], false, p);
   gstore(slot(mats, M_ALPHAXI), S.m[3], p);
+  emit_oz(oz, OZ_ALPHA, S.m[2], p, S.colexp);
+  emit_oz(oz, OZ_ALPHAXI, S.m[3], p, S.colexp);
   if (threadIdx.x == 0) ctrl->iter = m + 1;
 }
 
@@ -423,7 +436,7 @@ __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* m
 // plain: no QR; record ||R_{m+1}||_F^2 (trace of the Hermitian Gram) and, for block COCG,
 // beta = (R_m^T R_m)^{-1} R_{m+1}^T R_{m+1}.
 __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                             int plain) {
+                             int plain, uint2* oz) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   sum_stage1(stage1, ncomp, S.gs);
@@ -464,6 +477,7 @@ __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp,
   gstore(slot(mats, M_XI), S.m[4], p);
   gstore(slot(mats, M_TAU), S.m[1], p);
   gstore(slot(mats, M_TINV), S.m[2], p);
+  emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     const int E = tri_count(p);
     expand_tri(S.gs + 2 * E, S.m[0], p, false);       // W^T W
@@ -481,7 +495,7 @@ __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp,
 }
 
 // cocr after V_{m+1} (Algorithm 3, line 8): H+ = T^T (W^T A W) T, beta' = H^{-1} tau^T H+.
-__global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
+__global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, uint2* oz) {
   SMALL_PROLOGUE
   if (ctrl->done) return;
   sum_stage1(stage1, ncomp, S.gs);
@@ -502,6 +516,7 @@ __global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double
     return;
   }
   gstore(slot(mats, M_BETA), S.m[5], p);
+  emit_oz(oz, OZ_BETA, S.m[5], p, S.colexp);
 }
 
 // Norm of the residual from a norm-only residual pass (Sec. 3, true residual).
@@ -592,19 +607,19 @@ void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, 
 }
 
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
-                  double* hist, cudaStream_t s) {
+                  double* hist, cudaStream_t s, uint2* oz) {
   const size_t sm = small_smem();
   const int ncomp = 2 * ne;
   const int m = method & 15, plain = (method >> 4) & 1;   // method: 0 cocg / 1 cocr, +16 plain form
   switch (kind) {
-    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, plain); break;
+    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, plain, oz); break;
     case SK_SETUP_INNER:
-      k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, plain);
+      k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, plain, oz);
       break;
     case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
-    case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain); break;
-    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain); break;
-    case SK_COCR_BETA: k_small_cocr_beta<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
+    case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz); break;
+    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz); break;
+    case SK_COCR_BETA: k_small_cocr_beta<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, oz); break;
     case SK_TRR: k_small_trr<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, ctrl); break;
   }
 }

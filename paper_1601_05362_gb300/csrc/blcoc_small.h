@@ -9,8 +9,10 @@ enum SmallKind { SK_SETUP = 0, SK_COCR_H0, SK_ALPHA, SK_CHOL, SK_COCR_BETA, SK_T
 void prepare_small_kernels();
 // ctrl == nullptr: run even after the solve has finished (final residual pass).
 void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s);
+// oz != nullptr: also write the exact-slice fragments of the factors formed (tensor-core
+// applies of the FP64 path, p <= 16).
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
-                  double* hist, cudaStream_t s);
+                  double* hist, cudaStream_t s, uint2* oz = nullptr);
 void launch_sampled_grad(int64_t n, const int* rp, const int* ci, const double2* Lam, const double2* X, int p,
                          double2* out, int num_sms, cudaStream_t s);
 void launch_validate(int64_t n, int64_t nnz, const int* rp, const int* ci, const double2* va, int* flags, int which,

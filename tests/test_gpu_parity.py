@@ -267,3 +267,42 @@ def test_plain_block_methods_full_solve(method):
     dev = np.max(np.abs(info["hist"][:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m]))
     assert dev < max(HIST_TOL, 10 * hist_sens), (dev, hist_sens)
     assert info["relres_true"] < 1e-8
+
+
+@pytest.mark.parametrize("p", [5, 8, 13, 16])
+def test_fp64_tc_option_matches_oracle(p):
+    """Option fp64_tc: the p x p block updates run on the bf16 tensor cores by exact
+    integer slicing; the iterates must match the FP64 oracle like the FP64-FMA path."""
+    torch = need_gpu()
+    n = 1500 + 3 * p
+    A = P.random_complex_symmetric(n, 8, seed=100 + p, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(n, p, 200 + p)
+    X0 = 0.1 * P.complex_normal(n, p, 300 + p)
+    ref = O.bl_cocr_rq(A.to_scipy(), Bh, X0=X0, tol=0.0, maxit=12)
+    h = _handle(A)
+    h.set_option("fp64_tc", 1)
+    B = to_dev(torch, Bh)
+    X = to_dev(torch, X0)
+    assert h.solve(B, X, tol=0.0, maxit=12) == 5
+    hist = h.info()["hist"]
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
+    assert rel(X.cpu().numpy(), ref.X) < X_TOL
+    xi = h.xi(p)
+    assert np.max(np.abs(xi - ref.xi)) / np.linalg.norm(ref.xi) < HIST_TOL
+
+
+def test_fp64_tc_full_solve_helmholtz2d():
+    torch = need_gpu()
+    pr = P.helmholtz2d_n1024_p4("cocr_rq")
+    Bh = P.complex_normal(pr.n, 16, 9)
+    ref = O.bl_cocr_rq(pr.A.to_scipy(), Bh, tol=1e-10, maxit=500)
+    h = _handle(pr.A)
+    h.set_option("fp64_tc", 1)
+    B = to_dev(torch, Bh)
+    X = torch.zeros_like(B)
+    assert h.solve(B, X, tol=1e-10, maxit=500) == 0
+    info = h.info()
+    assert abs(info["iters"] - ref.iters) <= max(3, ref.iters // 20)
+    m = min(21, len(ref.hist))
+    assert np.max(np.abs(info["hist"][:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m])) < HIST_TOL
+    assert info["relres_true"] <= 1e-9
