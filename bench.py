@@ -38,8 +38,16 @@ MAXIT = 20000
 # FP64 peak of a GB300: 2 DFMA per clock per SM (nominal 1.25 TFLOP/s; a DFMA probe
 # on this pool measured 1.20 TFLOP/s at about 2.0 GHz) x 152 SMs x 2070 MHz max clock.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
-# Iterations the CPU oracle takes on this workload to 1e-10 (full oracle solve).
-ORACLE_ITERS_TO_TOL = None
+# Iterations the CPU oracle takes on this workload to 1e-10: the full oracle solve stored
+# by tests/golden/make_golden.py --full3d (bl_cocr_rq; 598 iterations).
+GOLDEN_FULL = os.path.join(ROOT, "tests", "golden", "helmholtz3d_n262144_p16.json")
+
+
+def oracle_iters_to_tol(method):
+    if method != "cocr_rq":
+        raise SystemExit("--impl reference: the oracle's iteration count is stored for bl_cocr_rq only")
+    with open(GOLDEN_FULL) as f:
+        return int(json.load(f)["iters"])
 
 
 def parse():
@@ -209,21 +217,27 @@ def _timed_solves(h, B, X, method, tol, maxit, reps, stream):
 
 
 def run_variants(h, B, X, pr, args, stream):
-    """Same-run measurements next to the headline (not part of it): Algorithm 3 with
-    U_{m+1} = A S_{m+1} formed by a second sparse product, on the headline workload; and
+    """Same-run measurements next to the headline (not part of it), on the headline
+    workload: Algorithm 3 with U_{m+1} = A S_{m+1} formed by a second sparse product, the
+    p x p block updates on the bf16 tensor cores by exact integer slicing (option fp64_tc),
+    and both together; and
     the mixed-precision refinement against plain FP64 on the 27-point random complex
     symmetric family (n = 262,144, p = 16), where complex64 inner solves converge."""
     import torch
     from paper_1601_05362_gb300 import blcoc, problems as P
     out = {}
-    h.set_option("u_explicit", 1)
-    _timed_solves(h, B, X, args.method, TOL, MAXIT, 1, stream)
-    r = _timed_solves(h, B, X, args.method, TOL, MAXIT, 2, stream)
-    h.set_option("u_explicit", 0)
-    r["value"] = pr.p / (r["ms_per_solve"] / 1e3)
-    r["unit"] = UNIT
-    r["workload"] = WORKLOAD
-    out["cocr_rq_explicit_U"] = r
+    for name, opts in (("explicit_U", {"u_explicit": 1}), ("fp64_tc", {"fp64_tc": 1}),
+                       ("fp64_tc_explicit_U", {"fp64_tc": 1, "u_explicit": 1})):
+        for k, v in opts.items():
+            h.set_option(k, v)
+        _timed_solves(h, B, X, args.method, TOL, MAXIT, 1, stream)
+        r = _timed_solves(h, B, X, args.method, TOL, MAXIT, 2, stream)
+        for k in opts:
+            h.set_option(k, 0)
+        r["value"] = pr.p / (r["ms_per_solve"] / 1e3)
+        r["unit"] = UNIT
+        r["workload"] = WORKLOAD
+        out[args.method + "_" + name] = r
     A2 = P.random_symmetric_27pt(64, 64, 64, seed=2)
     B2 = torch.from_numpy(P.complex_normal(A2.n, 16, 5)).cuda()
     X2 = torch.zeros_like(B2)
@@ -283,7 +297,7 @@ def run_reference(args):
     if rank != 0:
         return
     pr = problem(args.method)
-    iters_to_tol = ORACLE_ITERS_TO_TOL
+    iters_to_tol = oracle_iters_to_tol(args.method)
     sample_iters = 4
     samples = []
     for i in range(args.warmup + args.steps):
