@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--ncu-case", type=int, default=0, metavar="ITERS",
                     help="profiler case: one solve of the same workload for exactly ITERS iterations, then exit")
+    ap.add_argument("--option", action="append", default=[], metavar="KEY=VALUE",
+                    help="solver option for the profiler case (blcoc_set_option), e.g. fp64_tc=1")
     return ap.parse_args()
 
 
@@ -88,10 +90,14 @@ def algorithmic(pr):
     return flops, bytes_, a_bytes + 14 * nps, sum(flops.values())
 
 
+# The sources that define the row-pass kernels the traffic figures belong to.
+ROWPASS_SOURCES = ("blcoc_common.cuh", "blcoc_ozaki.cuh", "blcoc_rowpass.cuh", "kset_p16.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_05362_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in ROWPASS_SOURCES:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -478,6 +484,9 @@ def run_ncu_case(args):
     h = blcoc.Handle.from_csr(pr.A)
     B = torch.from_numpy(pr.B).cuda()
     X = torch.zeros_like(B)
+    for kv in args.option:
+        key, val = kv.split("=", 1)
+        h.set_option(key, int(val))
     st = h.solve(B, X, method=args.method, tol=0.0, maxit=args.ncu_case)
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case_iters": args.ncu_case, "status": blcoc.status_string(st),

@@ -126,6 +126,33 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
                                  double* ms_per_iter_out);
 
 /*
+ * blcoc_solve_batched_persistent - the same batch (arguments, results and statuses as
+ * blcoc_solve_batched; p[i] <= 16, rq methods) with every iteration of every system in
+ * ONE persistent kernel launch.  An iteration of Algorithm 2 or 3 (Sec. 2.2) is a chain
+ * of stages per system (row passes, their reductions, the p x p stages); the items of a
+ * stage (a row pass's 32-row chunk groups, the reduction slices, one p x p solve) wait in
+ * a ring of work items, the resident CTAs take them as they become ready, and the CTA
+ * that finishes a stage publishes the system's next one.  So systems advance
+ * independently (per-system work queues), one system's p x p stages overlap the others'
+ * row passes, and a system whose stopping test (top of an iteration) has fired publishes
+ * nothing more (convergence mask).  The launch and the copies that arm it are one CUDA
+ * graph (a direct launch if capture is refused; blcoc_get_stat(hs[0], "persistent_graph")
+ * says which).  Each system's iterates, history and residuals are bitwise those of a
+ * separate blcoc_solve.
+ * With autotune != 0, successive calls with the same batch signature (every system's n,
+ * nnz and p) time the candidate grid sizes (resident CTAs per SM) in turn and then keep
+ * the fastest per system-iteration; blcoc_last_error(hs[0]) names the shape used.
+ * Every wait of the kernel (for work, for a free ring slot) gives up after the option
+ * "persistent_timeout_ms" of hs[0] (default 10000 ms); the call then returns
+ * BLCOC_ERR_TIMEOUT (the handles stay usable; X holds an unfinished iterate).
+ * Scratch (a system table, the ring, counters) is allocated per call.  The paper has no
+ * batched form.
+ */
+blcoc_status blcoc_solve_batched_persistent(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
+                                            const int* p, blcoc_method method, double tol, int maxit, int autotune,
+                                            double* ms_per_iter_out);
+
+/*
  * blcoc_get_info - results of the last solve.
  *   iters            : number of iterations taken (the iterate X holds is X_iters).
  *   relres_recursive : ||xi_iters||_F / ||B||_F.
@@ -197,6 +224,11 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  computes them with FP64 FMAs.
  *   "u_explicit_mixed": the same for the complex64 inner solves of BLCOC_COCR_RQ_MIXED
  *                  (default 1: the recurrence drifts quickly in single precision).
+ *   "persistent_timeout_ms": blcoc_solve_batched_persistent (read from hs[0]): limit of
+ *                  one wait of the kernel, in [1, 600000] ms (default 10000).
+ *   "persistent_stall": blcoc_solve_batched_persistent (read from hs[0]), a test of the
+ *                  time limit: 1 publishes no first work item, so every wait for work
+ *                  runs out and the call returns BLCOC_ERR_TIMEOUT (0 = off, default).
  *   "timing"     : 1 brackets every kernel of the iterations with CUDA events on
  *                  the internal stream (also inside the graph) and accumulates per-kernel
  *                  device time; 0 (default) records nothing.
@@ -205,7 +237,8 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
 blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
 
 /* blcoc_get_stat - counters of the last solve: "launches" (kernels launched by the
- * solve, including those inside graph replays), "graph_replays", "outer_iters"
+ * solve, including those inside graph replays), "graph_replays", "outer_iters",
+ * "persistent_graph" (last persistent batch: 1 graph replays, 0 direct launches, -1 none)
  * (refinement steps of a mixed solve), and with the
  * "timing" option "kt_ns.<kernel>" (total device nanoseconds) and "kt_n.<kernel>"
  * (launches that did work) for <kernel> in resid, spmm_gram, spmm_plain, cocr_passA,

@@ -52,6 +52,8 @@ SIGNATURES = {
     "blcoc_sampled_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "blcoc_solve_batched": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                       C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "blcoc_solve_batched_persistent": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                                 C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "blcoc_destroy": (C.c_int, [C.c_void_p]),
     "blcoc_status_string": (C.c_char_p, [C.c_int]),
     "blcoc_last_error": (C.c_char_p, [C.c_void_p]),
@@ -276,9 +278,10 @@ class Handle:
         self.close()
 
 
-def solve_batched(handles, Bs, Xs, method="cocr_rq", tol=1e-10, maxit=None, autotune=True):
-    """blcoc_solve_batched over lists of Handles and device tensors; returns (status,
-    ms per system-iteration, autotune message)."""
+def solve_batched(handles, Bs, Xs, method="cocr_rq", tol=1e-10, maxit=None, autotune=True, persistent=False):
+    """blcoc_solve_batched (or, with persistent=True, blcoc_solve_batched_persistent) over
+    lists of Handles and device tensors; returns (status, ms per system-iteration, launch
+    shape message)."""
     lib = load_library()
     k = len(handles)
     if not (len(Bs) == len(Xs) == k):
@@ -294,8 +297,9 @@ def solve_batched(handles, Bs, Xs, method="cocr_rq", tol=1e-10, maxit=None, auto
     ps = (C.c_int * k)(*[int(b.shape[1]) for b in Bs])
     maxit = max(h.n for h in handles) if maxit is None else int(maxit)
     ms = C.c_double()
-    st = lib.blcoc_solve_batched(k, hs, bp, xp, ps, METHODS[method] if isinstance(method, str) else int(method),
-                                 float(tol), maxit, 1 if autotune else 0, C.byref(ms))
+    fn = lib.blcoc_solve_batched_persistent if persistent else lib.blcoc_solve_batched
+    st = fn(k, hs, bp, xp, ps, METHODS[method] if isinstance(method, str) else int(method),
+            float(tol), maxit, 1 if autotune else 0, C.byref(ms))
     msg = lib.blcoc_last_error(hs[0]).decode() if k else ""
     if st not in (BLCOC_OK, BLCOC_NOT_CONVERGED, BLCOC_BREAKDOWN):
         raise BlcocError(st, msg or lib.blcoc_last_error(None).decode())

@@ -11,6 +11,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -18,6 +20,7 @@
 #include "blcoc_common.cuh"
 #include "blcoc_ozaki.cuh"
 #include "blcoc_small.h"
+#include "blcoc_batched.h"
 
 using namespace blcoc;
 
@@ -116,6 +119,9 @@ struct blcoc_ctx {
   uint2* ozbuf = nullptr;     // their factor fragments
   int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
   int u_explicit_mixed = 1;   // the same for the complex64 inner solves
+  int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
+  int persistent_stall = 0;   // persistent batch, test hook: no first work item is published
+  int stat_persistent_graph = -1;   // last persistent batch: 1 graph replays, 0 direct launches
   Graph graph;
   // kernel timing: event pool and per-kind totals of the last solve
   std::vector<cudaEvent_t> evpool;
@@ -624,6 +630,16 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     (key[10] == 0 ? h->u_explicit : h->u_explicit_mixed) = (int)value;
     return BLCOC_OK;
   }
+  if (!strcmp(key, "persistent_timeout_ms")) {
+    if (value < 1 || value > 600000) return invalid(h, "persistent_timeout_ms must be in [1, 600000]");
+    h->persistent_timeout_ms = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "persistent_stall")) {
+    if (value != 0 && value != 1) return invalid(h, "persistent_stall must be 0 or 1");
+    h->persistent_stall = (int)value;
+    return BLCOC_OK;
+  }
   return invalid(h, "unknown option");
 }
 
@@ -632,6 +648,7 @@ blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value) {
   if (!strcmp(key, "launches")) { *value = h->stat_launches; return BLCOC_OK; }
   if (!strcmp(key, "graph_replays")) { *value = h->stat_replays; return BLCOC_OK; }
   if (!strcmp(key, "outer_iters")) { *value = h->outer_iters; return BLCOC_OK; }
+  if (!strcmp(key, "persistent_graph")) { *value = h->stat_persistent_graph; return BLCOC_OK; }
   for (int k = 0; k < kNumKinds; ++k) {
     const std::string nm(kKindNames[k]);
     if (("kt_ns." + nm) == key) { *value = (int64_t)(h->kt_ms[k] * 1e6); return BLCOC_OK; }
@@ -872,6 +889,220 @@ blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, 
 
 }  // namespace
 
+// ------------------------------------------------------------------------ batched solves
+namespace {
+
+// Launch shapes chosen by the batch autotuner, per batch signature (form, method, and
+// every system's n, nnz and p).
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;
+
+std::string tune_key(int form, int method, int nsys, const blcoc_handle* hs, const int* p) {
+  std::string k = std::to_string(form) + "/" + std::to_string(method);
+  for (int i = 0; i < nsys; ++i)
+    k += "/" + std::to_string(hs[i]->n) + "," + std::to_string(hs[i]->nnz) + "," + std::to_string(p[i]);
+  return k;
+}
+int tune_lookup(const std::string& k) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tune_cache.find(k);
+  return it == g_tune_cache.end() ? -1 : it->second;
+}
+void tune_store(const std::string& k, int v) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[k] = v;
+}
+
+// Iterations of a batch in the persistent kernel: one launch (with the copies that arm its
+// ring, scheduler state and per-system counters, captured as one CUDA graph) runs every
+// system until it stops.  Autotuning: successive calls with the same batch signature try
+// the candidate grid sizes (resident CTAs per SM) in turn, then keep the fastest per
+// system-iteration.
+struct PersTune {
+  std::vector<double> ms;   // per candidate; < 0: not tried yet
+};
+std::map<std::string, PersTune> g_pers_tune;
+
+blcoc_status iterate_persistent(int nsys, const blcoc_handle* hs, std::vector<Solver>& sv, std::vector<char>& live,
+                                const int* p, int method, int maxit, int autotune, const std::string& tkey,
+                                int64_t* launches, double* total_ms, int64_t* total_iters, std::string* shape_msg) {
+  (void)maxit;
+  blcoc_ctx* h0 = hs[0];
+  int pmax = 1, nlive = 0;
+  for (int i = 0; i < nsys; ++i) {
+    pmax = p[i] > pmax ? p[i] : pmax;
+    nlive += live[i] ? 1 : 0;
+  }
+  if (nlive == 0) return BLCOC_OK;
+  const size_t smem = persistent_smem(pmax);
+  int occ = 0;
+  CK(h0, persistent_ctas_per_sm(smem, &occ));
+  if (occ < 1) return invalid(h0, "batched (persistent): the kernel does not fit on an SM");
+  const int maxk = occ < 3 ? occ : 3;
+  std::vector<int> cand;   // resident CTAs per SM
+  for (int k = (maxk < 2 ? maxk : 2); k >= 1; --k) cand.push_back(k);
+  if (maxk == 3) cand.push_back(3);
+  int pick = 0, trying = -1;
+  if (autotune) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    PersTune& t = g_pers_tune[tkey];
+    if (t.ms.size() != cand.size()) t.ms.assign(cand.size(), -1.0);
+    for (size_t c = 0; c < cand.size() && trying < 0; ++c)
+      if (t.ms[c] < 0) trying = (int)c;
+    if (trying >= 0) {
+      pick = trying;
+    } else {
+      for (size_t c = 1; c < cand.size(); ++c)
+        if (t.ms[c] < t.ms[pick]) pick = (int)c;
+    }
+  }
+  const int G = cand[pick] * h0->num_sms;
+
+  std::vector<PersSys> hsys(nsys);
+  int64_t M = 0;
+  for (int i = 0; i < nsys; ++i) {
+    hsys[i].a = sv[i].base();
+    hsys[i].stage1 = hs[i]->stage1;
+    hsys[i].hist = hs[i]->hist;
+    hsys[i].pp = sv[i].PP;
+    const bool cocr = method == BLCOC_COCR_RQ;
+    hsys[i].vg[0] = sv[i].K->grid(hs[i]->n, cocr ? Solver::K_COCR_A : Solver::K_COCG_1, hs[i]->num_sms);
+    hsys[i].vg[1] = sv[i].K->grid(hs[i]->n, Solver::K_SPMM_GRAM, hs[i]->num_sms);
+    hsys[i].vg[2] = sv[i].K->grid(hs[i]->n, cocr ? Solver::K_COCR_C : Solver::K_COCG_2, hs[i]->num_sms);
+    int mx = RED_SPLIT;
+    for (int v : hsys[i].vg) mx = v > mx ? v : mx;
+    M += mx;
+  }
+  const unsigned cap = (unsigned)(2 * M + nsys + 64);
+  // pinned image of [scheduler state][per-system counters][ring]
+  const size_t off_run = sizeof(SchedState), off_ring = off_run + (size_t)nsys * sizeof(SysRun);
+  const size_t bytes = off_ring + (size_t)cap * sizeof(QItem);
+
+  cudaStream_t ms = nullptr;
+  PersSys* d_sys = nullptr;
+  unsigned char* d_buf = nullptr;
+  unsigned char* h_buf = nullptr;
+  SchedState* h_done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  blcoc_status st = BLCOC_OK;
+  do {
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&ms, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess ||
+        (e = cudaMalloc(&d_sys, nsys * sizeof(PersSys))) != cudaSuccess ||
+        (e = cudaMalloc(&d_buf, bytes)) != cudaSuccess ||
+        (e = cudaMallocHost(&h_buf, bytes + sizeof(SchedState))) != cudaSuccess) {
+      st = cuda_fail(h0, e, "batched (persistent): workspace");
+      break;
+    }
+    h_done = reinterpret_cast<SchedState*>(h_buf + bytes);
+    SchedState* hs0 = reinterpret_cast<SchedState*>(h_buf);
+    SysRun* hrun = reinterpret_cast<SysRun*>(h_buf + off_run);
+    QItem* hring = reinterpret_cast<QItem*>(h_buf + off_ring);
+    *hs0 = SchedState{};
+    for (unsigned k = 0; k < cap; ++k) hring[k] = QItem{~0ull, (unsigned long long)k, 0, 0, 0, 0};
+    unsigned long long tail = 0;
+    for (int i = 0; i < nsys; ++i) {
+      hrun[i] = SysRun{0, live[i] ? 1 : 0};
+      if (live[i] && !h0->persistent_stall) {   // the test hook publishes nothing: every wait runs out
+        hring[tail] = QItem{tail, tail, i, 0, 0, 0};
+        ++tail;
+      }
+    }
+    hs0->tail = tail;
+    hs0->active = nlive;
+    for (int i = 0; i < nsys; ++i) {   // the batch stream starts after every setup
+      if ((e = cudaEventRecord(hs[i]->ev, hs[i]->s)) != cudaSuccess || (e = cudaStreamWaitEvent(ms, hs[i]->ev, 0)) != cudaSuccess)
+        break;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sys, hsys.data(), nsys * sizeof(PersSys), cudaMemcpyHostToDevice, ms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ms);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h0, e, "batched (persistent): system table");
+      break;
+    }
+    SchedState* d_sch = reinterpret_cast<SchedState*>(d_buf);
+    SysRun* d_run = reinterpret_cast<SysRun*>(d_buf + off_run);
+    QItem* d_ring = reinterpret_cast<QItem*>(d_buf + off_ring);
+    const long long tmo = (long long)h0->persistent_timeout_ms * 1000000LL;
+    auto enqueue = [&]() -> cudaError_t {
+      cudaError_t r = cudaMemcpyAsync(d_buf, h_buf, bytes, cudaMemcpyHostToDevice, ms);
+      if (r == cudaSuccess) r = launch_persistent(d_sys, method, d_sch, d_ring, cap, d_run, tmo, G, smem, ms);
+      if (r == cudaSuccess) r = cudaMemcpyAsync(h_done, d_sch, sizeof(SchedState), cudaMemcpyDeviceToHost, ms);
+      return r;
+    };
+    bool use_graph = true;
+    {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(ms, cudaStreamCaptureModeThreadLocal);
+      cudaError_t e2 = e == cudaSuccess ? enqueue() : e;
+      cudaError_t e3 = e == cudaSuccess ? cudaStreamEndCapture(ms, &g) : e;
+      if (e2 == cudaSuccess && e3 == cudaSuccess) e3 = cudaGraphInstantiate(&exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e2 != cudaSuccess || e3 != cudaSuccess) {
+        use_graph = false;
+        exec = nullptr;
+        cudaGetLastError();
+      }
+    }
+    if ((e = cudaEventRecord(t0, ms)) != cudaSuccess) {
+      st = cuda_fail(h0, e, "batched (persistent): event");
+      break;
+    }
+    e = use_graph ? cudaGraphLaunch(exec, ms) : enqueue();
+    if (e == cudaSuccess) e = cudaEventRecord(t1, ms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ms);
+    if (e != cudaSuccess) {
+      st = cuda_fail(h0, e, "batched (persistent): launch");
+      break;
+    }
+    *launches += 1;
+    h0->stat_persistent_graph = use_graph ? 1 : 0;
+    if (h_done->err) {
+      h0->err = "batched (persistent): a wait for work exceeded persistent_timeout_ms";
+      st = BLCOC_ERR_TIMEOUT;
+      break;
+    }
+    float msr = 0.f;
+    cudaEventElapsedTime(&msr, t0, t1);
+    int64_t its = 0;
+    for (int i = 0; i < nsys; ++i) {
+      if (!live[i]) continue;
+      if ((e = cudaMemcpy(hs[i]->h_ctrl, hs[i]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+      its += hs[i]->h_ctrl->iter;
+      live[i] = 0;
+    }
+    if (e != cudaSuccess) {
+      st = cuda_fail(h0, e, "batched (persistent): control blocks");
+      break;
+    }
+    *total_ms += msr;
+    *total_iters += its;
+    if (autotune && its > 0) {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      PersTune& t = g_pers_tune[tkey];
+      if (trying >= 0) t.ms[trying] = msr / (double)its;
+    }
+    char buf[200];
+    snprintf(buf, sizeof buf, "persistent kernel: %d CTAs (%d per SM), dataflow work queue, %s%s", G, cand[pick],
+             use_graph ? "CUDA graph" : "direct launch",
+             autotune ? (trying >= 0 ? ", autotune: timing this candidate" : ", autotuned") : "");
+    *shape_msg = buf;
+  } while (false);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (ms) cudaStreamSynchronize(ms);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (d_sys) cudaFree(d_sys);
+  if (d_buf) cudaFree(d_buf);
+  if (h_buf) cudaFreeHost(h_buf);
+  if (ms) cudaStreamDestroy(ms);
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_method method, double tol, int maxit) {
@@ -994,9 +1225,9 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   }
 }
 
-blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
-                                 const int* p, blcoc_method method, double tol, int maxit, int autotune,
-                                 double* ms_per_iter_out) {
+static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* hs, const void* const* B,
+                                       void* const* X, const int* p, blcoc_method method, double tol, int maxit,
+                                       int autotune, double* ms_per_iter_out) {
   if (nsys < 1 || !hs || !B || !X || !p) return invalid(nullptr, "blcoc_solve_batched: NULL argument or nsys < 1");
   if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ) return invalid(nullptr, "batched: rq methods only");
   if (!(tol >= 0.0) || std::isinf(tol) || maxit < 0) return invalid(nullptr, "batched: bad tol or maxit");
@@ -1004,6 +1235,7 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
   for (int i = 0; i < nsys; ++i) {
     if (!hs[i] || hs[i]->dev != dev) return invalid(nullptr, "batched: handles must be non-NULL and on one device");
     if (p[i] < 1 || p[i] > BLCOC_MAX_P) return invalid(nullptr, "batched: p must be in [1, 32]");
+    if (form == 1 && p[i] > PERSISTENT_PMAX) return invalid(nullptr, "batched (persistent): p must be in [1, 16]");
     if (!B[i] || !X[i] || B[i] == X[i]) return invalid(nullptr, "batched: B[i], X[i] must be distinct device pointers");
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return invalid(nullptr, "batched: each system needs its own handle");
@@ -1049,108 +1281,130 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
     }
     CK(h, cudaGetLastError());
   }
-  cudaStream_t main_s = nullptr;
-  cudaEvent_t fork_ev = nullptr;
-  std::vector<cudaEvent_t> join(nsys, nullptr);
-  CK(h0, cudaStreamCreateWithFlags(&main_s, cudaStreamNonBlocking));
-  CK(h0, cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
-  for (auto& e : join) CK(h0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-  cudaEvent_t t0, t1;
-  CK(h0, cudaEventCreate(&t0));
-  CK(h0, cudaEventCreate(&t1));
-  for (int i = 0; i < nsys; ++i) {   // the batch stream starts after every setup
-    CK(h0, cudaEventRecord(join[i], hs[i]->s));
-    CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
-  }
-  // one graph: every live system's `poll` iterations as a parallel branch
-  auto capture = [&](int poll, int grid_sms, cudaGraphExec_t* exec, int* nlaunch) -> blcoc_status {
-    cudaGraph_t graph = nullptr;
-    CK(h0, cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
-    CK(h0, cudaEventRecord(fork_ev, main_s));
-    int launches = 0;
-    for (int i = 0; i < nsys; ++i) {
-      if (!live[i]) continue;
-      CK(h0, cudaStreamWaitEvent(hs[i]->s, fork_ev, 0));
-      sv[i].grid_sms = grid_sms;
-      const int before = sv[i].launches;
-      for (int k = 0; k < poll; ++k) sv[i].iteration();
-      launches += sv[i].launches - before;
-      sv[i].launches = before;
+  int64_t launches = 0;
+  double total_ms = 0.0;
+  int64_t total_iters = 0;
+  blcoc_status st = BLCOC_OK;
+  std::string shape_msg;
+  const std::string tkey = tune_key(form, (int)method, nsys, hs, p);
+  if (form == 0) {
+    cudaStream_t main_s = nullptr;
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join(nsys, nullptr);
+    CK(h0, cudaStreamCreateWithFlags(&main_s, cudaStreamNonBlocking));
+    CK(h0, cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    for (auto& e : join) CK(h0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t t0, t1;
+    CK(h0, cudaEventCreate(&t0));
+    CK(h0, cudaEventCreate(&t1));
+    for (int i = 0; i < nsys; ++i) {   // the batch stream starts after every setup
       CK(h0, cudaEventRecord(join[i], hs[i]->s));
       CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
     }
-    cudaError_t e = cudaStreamEndCapture(main_s, &graph);
-    if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaStreamEndCapture");
-    e = cudaGraphInstantiate(exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaGraphInstantiate");
-    *nlaunch = launches;
-    return BLCOC_OK;
-  };
-  // candidate launch shapes: grid sized for all / half / a quarter of the SMs (several
-  // systems then share the GPU), graph batches of 8, 16 or 32 iterations
-  struct Shape { int poll, grid_sms; };
-  std::vector<Shape> cand = {{16, h0->num_sms}};
-  if (autotune) cand = {{16, h0->num_sms}, {16, h0->num_sms / 2}, {16, h0->num_sms / 4}, {8, h0->num_sms / 2},
-                        {32, h0->num_sms / 2}};
-  size_t ci = 0;
-  int best = -1, cur = -1;
-  double best_ms = 1e300;
-  cudaGraphExec_t exec = nullptr;
-  int exec_launches = 0, exec_poll = 0;
-  double total_ms = 0.0;
-  int64_t total_iters = 0;
-  int64_t launches = 0;
-  blcoc_status st = BLCOC_OK;
-  for (int round = 0;; ++round) {
-    bool any = false;
-    for (int i = 0; i < nsys; ++i) any = any || live[i];
-    if (!any) break;
-    const int idx = (ci < cand.size()) ? (int)ci : best;
-    const Shape sh = cand[idx];
-    if (!exec || idx != cur) {   // (re)capture only when the launch shape changes
-      if (exec) cudaGraphExecDestroy(exec);
-      exec = nullptr;
-      st = capture(sh.poll, sh.grid_sms, &exec, &exec_launches);
-      if (st != BLCOC_OK) break;
-      exec_poll = sh.poll;
-      cur = idx;
-    }
-    std::vector<int> it_before(nsys);
-    for (int i = 0; i < nsys; ++i) it_before[i] = hs[i]->h_ctrl->iter;
-    CK(h0, cudaEventRecord(t0, main_s));
-    CK(h0, cudaGraphLaunch(exec, main_s));
-    CK(h0, cudaEventRecord(t1, main_s));
-    launches += exec_launches;
-    for (int i = 0; i < nsys; ++i)
-      if (live[i]) CK(h0, cudaMemcpyAsync(hs[i]->h_ctrl, hs[i]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, main_s));
-    CK(h0, cudaStreamSynchronize(main_s));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, t0, t1);
-    int64_t its = 0;
-    for (int i = 0; i < nsys; ++i)
-      if (live[i]) {
-        its += hs[i]->h_ctrl->iter - it_before[i];
-        if (hs[i]->h_ctrl->done) live[i] = 0;
-        if (round > (maxit + exec_poll) / (exec_poll > 0 ? exec_poll : 1) + 8) {
-          h0->err = "batched: iteration control did not stop";
-          st = BLCOC_ERR_CUDA;
+    // one graph: every live system's `poll` iterations as a parallel branch
+    auto capture = [&](int poll, int grid_sms, cudaGraphExec_t* exec, int* nlaunch) -> blcoc_status {
+      cudaGraph_t graph = nullptr;
+      CK(h0, cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
+      CK(h0, cudaEventRecord(fork_ev, main_s));
+      int launches = 0;
+      for (int i = 0; i < nsys; ++i) {
+        if (!live[i]) continue;
+        CK(h0, cudaStreamWaitEvent(hs[i]->s, fork_ev, 0));
+        sv[i].grid_sms = grid_sms;
+        const int before = sv[i].launches;
+        for (int k = 0; k < poll; ++k) sv[i].iteration();
+        launches += sv[i].launches - before;
+        sv[i].launches = before;
+        CK(h0, cudaEventRecord(join[i], hs[i]->s));
+        CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
+      }
+      cudaError_t e = cudaStreamEndCapture(main_s, &graph);
+      if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaStreamEndCapture");
+      e = cudaGraphInstantiate(exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaGraphInstantiate");
+      *nlaunch = launches;
+      return BLCOC_OK;
+    };
+    // candidate launch shapes: grid sized for all / half / a quarter of the SMs (several
+    // systems then share the GPU), graph batches of 8, 16 or 32 iterations
+    struct Shape { int poll, grid_sms; };
+    std::vector<Shape> cand = {{16, h0->num_sms}};
+    if (autotune) cand = {{16, h0->num_sms}, {16, h0->num_sms / 2}, {16, h0->num_sms / 4}, {8, h0->num_sms / 2},
+                          {32, h0->num_sms / 2}};
+    const int cached = autotune ? tune_lookup(tkey) : -1;
+    if (cached >= 0 && cached < (int)cand.size()) cand = {cand[cached]};
+    size_t ci = 0;
+    int best = -1, cur = -1;
+    double best_ms = 1e300;
+    cudaGraphExec_t exec = nullptr;
+    int exec_launches = 0, exec_poll = 0;
+    for (int round = 0;; ++round) {
+      bool any = false;
+      for (int i = 0; i < nsys; ++i) any = any || live[i];
+      if (!any) break;
+      const int idx = (ci < cand.size()) ? (int)ci : best;
+      const Shape sh = cand[idx];
+      if (!exec || idx != cur) {   // (re)capture only when the launch shape changes
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        st = capture(sh.poll, sh.grid_sms, &exec, &exec_launches);
+        if (st != BLCOC_OK) break;
+        exec_poll = sh.poll;
+        cur = idx;
+      }
+      std::vector<int> it_before(nsys);
+      for (int i = 0; i < nsys; ++i) it_before[i] = hs[i]->h_ctrl->iter;
+      CK(h0, cudaEventRecord(t0, main_s));
+      CK(h0, cudaGraphLaunch(exec, main_s));
+      CK(h0, cudaEventRecord(t1, main_s));
+      launches += exec_launches;
+      for (int i = 0; i < nsys; ++i)
+        if (live[i]) CK(h0, cudaMemcpyAsync(hs[i]->h_ctrl, hs[i]->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, main_s));
+      CK(h0, cudaStreamSynchronize(main_s));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      int64_t its = 0;
+      for (int i = 0; i < nsys; ++i)
+        if (live[i]) {
+          its += hs[i]->h_ctrl->iter - it_before[i];
+          if (hs[i]->h_ctrl->done) live[i] = 0;
+          if (round > (maxit + exec_poll) / (exec_poll > 0 ? exec_poll : 1) + 8) {
+            h0->err = "batched: iteration control did not stop";
+            st = BLCOC_ERR_CUDA;
+          }
         }
+      total_ms += ms;
+      total_iters += its;
+      if (ci < cand.size()) {   // autotuning round: time per system-iteration
+        const double per = its > 0 ? ms / (double)its : 1e300;
+        if (per < best_ms) {
+          best_ms = per;
+          best = (int)ci;
+        }
+        ++ci;
       }
-    total_ms += ms;
-    total_iters += its;
-    if (ci < cand.size()) {   // autotuning round: time per system-iteration
-      const double per = its > 0 ? ms / (double)its : 1e300;
-      if (per < best_ms) {
-        best_ms = per;
-        best = (int)ci;
-      }
-      ++ci;
+      if (st != BLCOC_OK) break;
     }
-    if (st != BLCOC_OK) break;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (autotune && cached < 0 && best >= 0 && st == BLCOC_OK) tune_store(tkey, best);
+    if (best >= 0) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "autotuned launch shape: graph batch %d iterations, grid for %d SMs",
+               cand[best].poll, cand[best].grid_sms);
+      shape_msg = buf;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (auto& e : join) cudaEventDestroy(e);
+    cudaEventDestroy(fork_ev);
+    cudaStreamDestroy(main_s);
+    if (ms_per_iter_out) *ms_per_iter_out = total_iters > 0 ? total_ms / (double)total_iters : 0.0;
+  } else {
+    st = iterate_persistent(nsys, hs, sv, live, p, (int)method, maxit, autotune, tkey, &launches, &total_ms,
+                            &total_iters, &shape_msg);
+    if (ms_per_iter_out) *ms_per_iter_out = total_iters > 0 ? total_ms / (double)total_iters : 0.0;
   }
-  if (exec) cudaGraphExecDestroy(exec);
-  if (ms_per_iter_out) *ms_per_iter_out = total_iters > 0 ? total_ms / (double)total_iters : 0.0;
   // finish every system like a single solve: true residual, history, status
   blcoc_status worst = st;
   for (int i = 0; i < nsys && st == BLCOC_OK; ++i) {
@@ -1175,18 +1429,20 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
     blcoc_status si = c.done == 1 || nb == 0 ? BLCOC_OK : (c.done == 2 ? BLCOC_NOT_CONVERGED : BLCOC_BREAKDOWN);
     if (si != BLCOC_OK && worst == BLCOC_OK) worst = si;
   }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  for (auto& e : join) cudaEventDestroy(e);
-  cudaEventDestroy(fork_ev);
-  cudaStreamDestroy(main_s);
-  if (best >= 0 && h0) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "autotuned launch shape: graph batch %d iterations, grid for %d SMs",
-             cand[best].poll, cand[best].grid_sms);
-    if (worst == BLCOC_OK) h0->err = buf;
-  }
+  if (!shape_msg.empty() && worst == BLCOC_OK && h0) h0->err = shape_msg;
   return worst;
+}
+
+blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
+                                 const int* p, blcoc_method method, double tol, int maxit, int autotune,
+                                 double* ms_per_iter_out) {
+  return solve_batched_impl(0, nsys, hs, B, X, p, method, tol, maxit, autotune, ms_per_iter_out);
+}
+
+blcoc_status blcoc_solve_batched_persistent(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
+                                            const int* p, blcoc_method method, double tol, int maxit, int autotune,
+                                            double* ms_per_iter_out) {
+  return solve_batched_impl(1, nsys, hs, B, X, p, method, tol, maxit, autotune, ms_per_iter_out);
 }
 
 blcoc_status blcoc_get_info(blcoc_handle h, int* iters, double* relres_recursive, double* relres_true, double* hist,

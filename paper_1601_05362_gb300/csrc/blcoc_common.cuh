@@ -13,6 +13,17 @@ constexpr int NWARP = 4;        // warps per CTA in the row-pass kernels (one pe
 constexpr int RED_SPLIT = 16;   // first-stage slices of the cross-CTA Gram reduction
 constexpr int SMALL_THREADS = 256;
 
+// Loads of data that another CTA of the same launch may have written (blocks, factors,
+// partial sums, the control block).  The translation unit of the persistent batched
+// kernel defines BLCOC_COHERENT_LOADS before including this header: such loads then read
+// L2 (ld.global.cg) and can never be served by the non-coherent read-only path or by a
+// stale L1 line of an earlier phase.  Everywhere else they are plain loads.
+#ifdef BLCOC_COHERENT_LOADS
+#define BLCOC_LD(ptr) __ldcg(ptr)
+#else
+#define BLCOC_LD(ptr) (*(ptr))
+#endif
+
 // Device-resident control block of one solve.  Kernels of an iteration return at once
 // when `done` is non-zero, so a batch of queued iterations past convergence is a no-op.
 struct Ctrl {

@@ -57,7 +57,7 @@ __device__ __forceinline__ void load_tile(C* t, const C* __restrict__ g, int64_t
   const C* src = g + r0 * p;
   for (int e = lane; e < total; e += 32) {
     const int r = e / p, k = e - r * p;
-    t[tix(k, r)] = (e < valid) ? src[e] : czero<C>();
+    t[tix(k, r)] = (e < valid) ? BLCOC_LD(src + e) : czero<C>();
   }
 }
 
@@ -91,7 +91,7 @@ template <int PP, typename C>
 __device__ __forceinline__ void load_mat(C* s, const double2* __restrict__ g, int p) {
   for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
     const int k = e / PP, j = e - k * PP;
-    s[e] = (k < p && j < p) ? from_d2<C>(g[k * p + j]) : czero<C>();
+    s[e] = (k < p && j < p) ? from_d2<C>(BLCOC_LD(g + k * p + j)) : czero<C>();
   }
 }
 
@@ -313,7 +313,7 @@ __device__ __forceinline__ void gather_rows(C* Yt, const CsrDev& A, const C* __r
     C acc = czero<C>();
     if (row < A.n && k < p) {
       if constexpr (RESID) {
-        acc = Bg[row * p + k];
+        acc = BLCOC_LD(Bg + row * p + k);
         sb = fma((double)acc.x, (double)acc.x, sb);
         sb = fma((double)acc.y, (double)acc.y, sb);
       }
@@ -321,7 +321,7 @@ __device__ __forceinline__ void gather_rows(C* Yt, const CsrDev& A, const C* __r
       for (int j = beg; j < end; ++j) {
         const int c = __ldg(A.ci + j);
         const C av = __ldg(va + j);
-        const C x = Xg[(int64_t)c * p + k];
+        const C x = BLCOC_LD(Xg + (int64_t)c * p + k);
         if constexpr (RESID) cmsub(acc, av, x);
         else cmac(acc, av, x);
       }
@@ -348,14 +348,14 @@ constexpr int F_UEXPL = 4;      // explicit-U variant: SpMM gram Y^T Y; pass C w
 constexpr int F_FORCE = 16;     // run even when the control block says the solve is done
 
 #define BLCOC_PROLOGUE(CT)                                          \
-  if (!(a.flag & F_FORCE) && a.ctrl->done) return;                  \
+  if (!(a.flag & F_FORCE) && BLCOC_LD(&a.ctrl->done)) return;       \
   extern __shared__ __align__(16) unsigned char smem_raw[];         \
   CT* smem = reinterpret_cast<CT*>(smem_raw);                       \
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;       \
   const int64_t n = a.A.n;                                          \
   const int p = a.p;                                                \
   const int64_t nchunks = (n + CHUNK - 1) / CHUNK;                  \
-  const int64_t cstride = (int64_t)gridDim.x * NWARP;
+  const int64_t cstride = (int64_t)vgrid * NWARP;
 
 template <typename C>
 __device__ __forceinline__ C* blk(double2* p) { return reinterpret_cast<C*>(p); }
@@ -369,7 +369,7 @@ __device__ __forceinline__ const typename Cx<S>::T* vals_of(const CsrDev& A) {
 // the working precision S.  flag&1: norms only; flag&2: also R^T R (cocg).
 // Partials: [R^H R tri][R^T R tri][sum|B|^2, sum|R|^2]
 template <int PP, typename S>
-__global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
+__device__ __forceinline__ void d_resid(const PassArgs& a, const int vblk, const int vgrid) {
   BLCOC_PROLOGUE(double2)
   using G = Geo<PP>;
   const bool norm_only = a.flag & F_FIRST, sym2 = a.flag & F_SYM2;
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
   gh.init(G_HERM, p, lane);
   gs.init(G_SYM, p, lane);
   double sb = 0.0, sr = 0.0;
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     gather_rows<PP, double2, true>(tR, a.A, a.A.va, a.X, a.B, r0, p, lane, sb, sr);
     if (!norm_only) {
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
   sb = warp_sum_fixed(sb);
   sr = warp_sum_fixed(sr);
   __syncthreads();
-  double2* out = a.partials + (int64_t)blockIdx.x * a.ne;
+  double2* out = a.partials + (int64_t)vblk * a.ne;
   const int E = tri_count(p);
   if (!norm_only) {
     cta_write_gram(gh, red, out, warp, lane);
@@ -408,13 +408,17 @@ __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
     out[2 * E] = s;
   }
 }
+template <int PP, typename S>
+__global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
+  d_resid<PP, S>(a, blockIdx.x, gridDim.x);
+}
 
 // Y = A W over the chunk, W = the block in a.W; gram W^T Y (symmetric since A = A^T);
 // out = Y T (flag=1, cocr: V = A Q = (A W) tau^{-1}) or out = Y (flag=0, cocg: a.W = S,
 // out = A S).  flag&F_UEXPL: gram Y^T Y instead (explicit U = A S and U^T U).
 // Partials: [W^T Y or Y^T Y tri].
 template <int PP, typename S, bool OZ = false>
-__global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
+__device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
@@ -431,7 +435,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
   GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
   double dummy0 = 0.0, dummy1 = 0.0;
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     gather_rows<PP, C, false>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
     load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
@@ -450,18 +454,22 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+}
+template <int PP, typename S, bool OZ = false>
+__global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
+  d_spmm_gram<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 
 // Y = A W, nothing else (blcoc_spmm).
 template <int PP, typename S>
-__global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
+__device__ __forceinline__ void d_spmm_plain(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   C* tY = smem + warp * G::TILE;
   double d0 = 0.0, d1 = 0.0;
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     gather_rows<PP, C, false>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, d0, d1);
     __syncwarp();
@@ -469,11 +477,15 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
     __syncwarp();
   }
 }
+template <int PP, typename S>
+__global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
+  d_spmm_plain<PP, S>(a, blockIdx.x, gridDim.x);
+}
 
 // bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): W_{m+1} = Q_m - U_m alpha'_m
 // (Q_m stored by the previous pass C); gram W^H W for the Cholesky QR.
 template <int PP, typename S, bool OZ = false>
-__global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
+__device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
@@ -488,7 +500,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
   Fac<PP, S> AL{G::MATS_SMEM ? mA : reinterpret_cast<const C*>(a.mats + M_ALPHA * PMAX * PMAX), p};
   GramAcc<G::NTRI, S> g;
   g.init(G_HERM, p, lane);
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(tW, blk<C>(a.Q), r0, n, p, lane);
     load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
@@ -505,7 +517,11 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+}
+template <int PP, typename S, bool OZ = false>
+__global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
+  d_cocr_passA<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 
 // bl_cocr_rq pass C (Algorithm 3, lines 5, 9, 10) with Q_{m+1} = W_{m+1} T_{m+1} (stored
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
 // flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.  flag&F_UEXPL: no U update
 // and no gram (U_{m+1} = A S_{m+1} is formed by the SpMM that follows).
 template <int PP, typename S, bool OZ = false>
-__global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
+__device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
@@ -539,7 +555,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
   GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
     if (!first) {
@@ -597,14 +613,18 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   }
   if (uexpl) return;
   __syncthreads();
-  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)blockIdx.x * a.ne, warp, lane);
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+}
+template <int PP, typename S, bool OZ = false>
+__global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
+  d_cocr_passC<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 
 // bl_cocg_rq pass 1 (Algorithm 2, lines 5-6), Q_m stored by the previous pass 2:
 //   W_{m+1} = Q_m - (A S_m) alpha'_m;  X_{m+1} = X_m + S_m (alpha'_m xi_m);
 //   grams W^H W (QR) and W^T W (Q^T Q of line 7).  Partials: [W^H W tri][W^T W tri].
 template <int PP, typename S>
-__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
+__device__ __forceinline__ void d_cocg_pass1(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
@@ -624,7 +644,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
   GramAcc<G::NTRI, S> gh, gs;
   gh.init(G_HERM, p, lane);
   gs.init(G_SYM, p, lane);
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(b0, blk<C>(a.Q), r0, n, p, lane);
     load_tile<PP>(b1, blk<C>(a.V), r0, n, p, lane);
@@ -643,15 +663,19 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
     __syncwarp();
   }
   __syncthreads();
-  double2* out = a.partials + (int64_t)blockIdx.x * a.ne;
+  double2* out = a.partials + (int64_t)vblk * a.ne;
   cta_write_gram(gh, reinterpret_cast<double2*>(tiles), out, warp, lane);
   cta_write_gram(gs, reinterpret_cast<double2*>(tiles), out + tri_count(p), warp, lane);
+}
+template <int PP, typename S>
+__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
+  d_cocg_pass1<PP, S>(a, blockIdx.x, gridDim.x);
 }
 
 // bl_cocg_rq pass 2 (Algorithm 2, line 8): Q_{m+1} = W_{m+1} T_{m+1} (stored for the next
 // pass 1), S_{m+1} = Q_{m+1} + S_m beta'_m.  flag=1 (setup, line 2): S_0 = Q_0 = W_0 T_0.
 template <int PP, typename S>
-__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
+__device__ __forceinline__ void d_cocg_pass2(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
@@ -668,7 +692,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
   }
   Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
   Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
-  for (int64_t c = (int64_t)blockIdx.x * NWARP + warp; c < nchunks; c += cstride) {
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
     if (!first) load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
@@ -682,6 +706,10 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
     store_tile<PP>(blk<C>(a.S), b0, r0, n, p, lane);
     __syncwarp();
   }
+}
+template <int PP, typename S>
+__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
+  d_cocg_pass2<PP, S>(a, blockIdx.x, gridDim.x);
 }
 
 // Refinement update of the mixed-precision form: X (FP64) += D (working precision, held
