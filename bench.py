@@ -90,8 +90,9 @@ def algorithmic(pr):
     return flops, bytes_, a_bytes + 14 * nps, sum(flops.values())
 
 
-# The sources that define the row-pass kernels the traffic figures belong to.
-ROWPASS_SOURCES = ("blcoc_common.cuh", "blcoc_ozaki.cuh", "blcoc_rowpass.cuh", "kset_p16.cu")
+# The sources that define the FP64 row-pass kernels the traffic figures belong to (the
+# tensor-core header is compiled into the same unit but not into these kernels).
+ROWPASS_SOURCES = ("blcoc_common.cuh", "blcoc_rowpass.cuh", "kset_p16.cu")
 
 
 def source_hash():
@@ -258,7 +259,41 @@ def run_variants(h, B, X, pr, args, stream):
             r["workload"] = "random27pt_64cube_p16 (27-point pattern, 10% pairs dropped, diag 4+0.5i)"
             out[name + "_random27pt"] = r
     out["autograd_random27pt_n1048576_p8"] = run_autograd_variant(stream)
+    out["cocr_rq_helmholtz3d_128cube_p32_fixed_iters"] = run_large_variant(args, stream)
     return out
+
+
+def run_large_variant(args, stream, iters=24, warm=4):
+    """The n >= 2M case: 3D Helmholtz 128^3 (n = 2,097,152, k = 40), p = 32, FP64
+    bl_cocr_rq.  A full solve takes minutes, so this times a fixed iteration count: the
+    per-iteration time is (t(warm + iters) - t(warm)) / iters with CUDA events, against
+    the algorithmic FP64 flops and HBM bytes of one iteration."""
+    import torch
+    from paper_1601_05362_gb300 import blcoc, problems as P
+    pr = P.helmholtz3d_n2097152_p32(args.method)
+    B = torch.from_numpy(pr.B).cuda()
+    X = torch.zeros_like(B)
+    ms = {}
+    with blcoc.Handle.from_csr(pr.A) as h:
+        for m in (warm, warm + iters, warm, warm + iters):
+            X.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.solve(B, X, method=args.method, tol=0.0, maxit=m)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[m] = e0.elapsed_time(e1)
+        relres = h.info(hist_len=1)["relres"]
+    t_iter = (ms[warm + iters] - ms[warm]) / iters / 1e3
+    _, _, it_bytes, it_flops = algorithmic(pr)
+    del B, X
+    torch.cuda.empty_cache()
+    return {"n": pr.n, "nnz": pr.A.nnz, "p": pr.p, "iters_timed": iters, "ms_per_iter": t_iter * 1e3,
+            "alg_fp64_tflops": it_flops / t_iter / 1e12, "frac_of_fp64_peak": it_flops / t_iter / 1e12 / FP64_PEAK_TFLOPS,
+            "alg_bytes_per_iter": it_bytes, "alg_hbm_gbs": it_bytes / t_iter / 1e9,
+            "relres_after": relres}
 
 
 def run_autograd_variant(stream):
@@ -356,7 +391,7 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         solve_once()
-    h.set_option("timing", 1)
+    h.set_option("timing", 2)        # events around the row-pass kernels only (the roofline's)
     solve_once()                     # capture the timed graph once, outside the timed region
     kt = {}
     launches = 0

@@ -315,11 +315,12 @@ struct Solver {
       timers->push_back(t);
     }
   }
+  bool time_small = true;   // with timers: also bracket the reductions and p x p stages
   void reduce(int ne, const Ctrl* ctrl) {
     Timer t;
-    timed_begin(t, kKindReduce);
+    if (time_small) timed_begin(t, kKindReduce);
     launch_reduce(h->partials, last_grid, ne, h->stage1, ctrl, h->s);
-    timed_end(t);
+    if (time_small) timed_end(t);
     ++launches;
   }
   int plain = 0;   // 1: plain block method (Algorithm 1 / derived block COCG)
@@ -328,9 +329,9 @@ struct Solver {
   int sms() const { return grid_sms > 0 ? grid_sms : h->num_sms; }
   void small(SmallKind k, int ne) {
     Timer t;
-    timed_begin(t, kKindSmall0 + (int)k);
+    if (time_small) timed_begin(t, kKindSmall0 + (int)k);
     launch_small(k, p, method + 16 * plain, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s, oz);
-    timed_end(t);
+    if (time_small) timed_end(t);
     ++launches;
   }
   // kinds must match PassKind in blcoc_rowpass.cuh
@@ -592,7 +593,7 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     return BLCOC_OK;
   }
   if (!strcmp(key, "timing")) {
-    if (value != 0 && value != 1) return invalid(h, "timing must be 0 or 1");
+    if (value < 0 || value > 2) return invalid(h, "timing must be 0, 1 or 2");
     if (h->timing != (int)value) h->graph.reset();
     h->timing = (int)value;
     return BLCOC_OK;
@@ -722,6 +723,7 @@ blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
       CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
       const int before = sv.launches;
       sv.timers = h->timing ? &g.timers : nullptr;
+      sv.time_small = h->timing == 1;
       sv.capturing = true;
       for (int i = 0; i < batch; ++i) {
         sv.batch_iter = i;
@@ -760,6 +762,7 @@ blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
       if (h->timing) {
         h->evnext = 0;
         sv.timers = &direct_timers;
+        sv.time_small = h->timing == 1;
       }
       for (int i = 0; i < batch; ++i) {
         sv.batch_iter = i;
