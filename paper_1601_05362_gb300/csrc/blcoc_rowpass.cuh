@@ -751,12 +751,44 @@ constexpr size_t pass_smem(int kind) {
   return s;
 }
 
-template <int PP, typename S>
+// The pass kernel of one kind (OZ: the tensor-core variant where one exists).
+template <int PP, typename S, bool OZ>
+const void* pass_kernel(int kind) {
+  switch (kind) {
+    case K_RESID: return (const void*)k_resid<PP, S>;
+    case K_SPMM_GRAM: return (const void*)k_spmm_gram<PP, S, OZ>;
+    case K_SPMM_PLAIN: return (const void*)k_spmm_plain<PP, S>;
+    case K_COCR_A: return (const void*)k_cocr_passA<PP, S, OZ>;
+    case K_COCR_C: return (const void*)k_cocr_passC<PP, S, OZ>;
+    case K_COCG_1: return (const void*)k_cocg_pass1<PP, S>;
+    case K_COCG_2: return (const void*)k_cocg_pass2<PP, S>;
+    default: return nullptr;
+  }
+}
+
+// One wave of CTAs: SMs x the CTAs per SM the kernel's registers AND shared memory allow
+// (occupancy of that exact kernel, cached per device; at most 4), or fewer when the rows
+// need fewer.  Call after the kernel set's prepare() (shared-memory limits).
+template <int PP, typename S, bool OZ>
 int pass_grid(int64_t n, int kind, int num_sms) {
   if (kind == K_AXPY) return num_sms * 4;
-  const size_t smem = pass_smem<PP, S>(kind);
-  int per_sm = (int)((227u * 1024u) / (smem + 1024u));
-  per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+  static int cache[64][K_NKIND] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int per_sm = (dev >= 0 && dev < 64) ? cache[dev][kind] : 0;
+  if (per_sm == 0) {
+    const size_t smem = pass_smem<PP, S>(kind);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<PP, S, OZ>(kind), NWARP * 32, smem) ==
+            cudaSuccess &&
+        per_sm > 0) {
+      per_sm = per_sm > 4 ? 4 : per_sm;
+      if (dev >= 0 && dev < 64) cache[dev][kind] = per_sm;
+    } else {   // shared-memory limit not raised yet: shared memory alone decides, uncached
+      cudaGetLastError();
+      per_sm = (int)((227u * 1024u) / (smem + 1024u));
+      per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    }
+  }
   const int64_t nchunks = (n + CHUNK - 1) / CHUNK;
   int64_t want = (nchunks + NWARP - 1) / NWARP;
   int64_t g = (int64_t)num_sms * per_sm;
@@ -803,7 +835,7 @@ const KernelSet& kernel_set() {
       &launch_pass<PP, S, K_COCG_1, k_cocg_pass1<PP, S>>,
       &launch_pass<PP, S, K_COCG_2, k_cocg_pass2<PP, S>>,
       &launch_pass<PP, S, K_AXPY, k_axpy<PP, S>>,
-      &pass_grid<PP, S>,
+      &pass_grid<PP, S, false>,
       &prepare_pass_kernels<PP, S>,
   };
   return ks;
@@ -836,7 +868,7 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
-      &pass_grid<PP, double>,
+      &pass_grid<PP, double, true>,
       &prepare_pass_kernels_tc<PP>,
   };
   return ks;

@@ -82,14 +82,21 @@ def test_full_solve_properties(problem):
 
 
 def test_fp64_tc_first_iterations_and_solve(problem):
-    """The tensor-core (exact-slice) applies at the bench size: history against the
-    oracle for m <= 20 and X_5; then a full solve to the tolerance."""
+    """The tensor-core (exact-slice) applies at the bench size: X_5 against the oracle to
+    1e-10, the history for m <= 20 within max(1e-8, 10x the oracle's own sensitivity);
+    then a full solve to the tolerance."""
     torch = need_gpu()
     from paper_1601_05362_gb300 import blcoc
     pr = problem
     A = pr.A.to_scipy()
     ref = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=20)
     ref5 = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=5)
+    # the oracle's own history sensitivity to a rounding-level perturbation of B: the
+    # slice products round differently from FMAs, and this indefinite problem amplifies
+    # any rounding difference (the same bound the FP64 test applies to X_20)
+    Bp = pr.B * (1.0 + 1e-16 * np.random.default_rng(0).standard_normal(pr.B.shape))
+    hp = np.array(O.bl_cocr_rq(A, Bp, tol=0.0, maxit=20).hist)
+    hsens = np.max(np.abs(hp - np.array(ref.hist)) / np.array(ref.hist))
     with blcoc.Handle.from_csr(pr.A) as h:
         h.set_option("fp64_tc", 1)
         B = to_dev(torch, pr.B)
@@ -99,7 +106,8 @@ def test_fp64_tc_first_iterations_and_solve(problem):
         X.zero_()
         assert h.solve(B, X, tol=0.0, maxit=20) == blcoc.BLCOC_NOT_CONVERGED
         hist = np.asarray(h.info()["hist"])
-        assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8
+        herr = np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist))
+        assert herr < max(1e-8, 10 * hsens), (herr, hsens)
         X.zero_()
         assert h.solve(B, X, tol=pr.tol, maxit=pr.maxit) == blcoc.BLCOC_OK
         info = h.info()
