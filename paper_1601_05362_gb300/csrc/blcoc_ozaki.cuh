@@ -240,4 +240,182 @@ __device__ __forceinline__ void oz_apply(double2* out, const double2* base, cons
   }
 }
 
+// ------------------------------------------------------------------------------ Grams
+// FP64-accurate Gram of one warp's 32-row chunk on the tensor cores: P = Y'^T Z' with
+// Y' = [Yr | Yi], Z' = [Zr | Zi] (32 x 2p real), K = the 32 rows.  Every column of Y' and of
+// Z' is scaled by a power of two above its largest magnitude in the chunk and cut into
+// eight 7-bit digits, as in oz_apply; a level sums at most 8 slice pairs over K = 32 terms
+// (< 2^22, exact in fp32).  Each chunk's P is recombined to doubles (C-fragment order of
+// mma.m16n8k16) and added to the warp's running FP64 sums, which live in shared memory
+// between chunks.  The complex Gram follows from the four real blocks of P:
+//   Y^T Z = (P11 - P22) + i (P12 + P21),   Y^H Z = (P11 + P22) + i (P12 - P21).
+template <int PP>
+struct OzGramGeo {
+  static constexpr int NR = 2 * PP;        // real columns
+  static constexpr int MT = NR / 16;       // m16 tiles (rows of P)
+  static constexpr int NT = NR / 8;        // n8 tiles (columns of P)
+  static constexpr int NTILE = MT * NT;
+  static constexpr int ACC = NTILE * 4 * 32;   // doubles of one warp's running sums
+};
+
+// largest biased exponent of real column m (< 2PP) of [Tr | Ti] over the chunk's 32 rows;
+// lane m returns it (other lanes 0)
+template <int PP>
+__device__ __forceinline__ int oz_tile_colexp(const double2* T, int p, int lane) {
+  int eb = 0;
+  const int kc = lane % PP;
+  if (lane < 2 * PP && kc < p) {
+    const bool im = lane >= PP;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+      const double2 v = T[kc * 32 + (r ^ (kc & 7))];
+      eb = max(eb, oz_bexp(im ? v.y : v.x));
+    }
+  }
+  return eb;
+}
+
+// real entry (row r, real column m) of [Tr | Ti], zero for columns >= p
+template <int PP>
+__device__ __forceinline__ double oz_tile_val(const double2* T, int p, int r, int m) {
+  const int kc = m % PP;
+  if (kc >= p) return 0.0;
+  const double2 v = T[kc * 32 + (r ^ (kc & 7))];
+  return m >= PP ? v.y : v.x;
+}
+
+// exact level sums -> double: value = (hi 2^-42 + lo 2^-70) 2^(e_r + f_c), e = eb - 1022
+__device__ __forceinline__ double oz_recombine(const float (&acc)[OZ_NLEV][4], int o, int ebr, int ebc) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int L = 2; L <= 6; ++L) hi += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (6 - L));
+#pragma unroll
+  for (int L = 7; L <= OZ_LMAX; ++L) lo += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (10 - L));
+  const int sc = (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022) - 42;
+  double v = fma((double)lo, 0x1p-28, (double)hi);
+  if (ebr == 2047 || ebc == 2047) return __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
+  if (sc >= -1020 && sc <= 1020) return v * __longlong_as_double((long long)(sc + 1023) << 52);
+  return ldexp(v, sc);
+}
+
+// sums[tile][o][lane] += P of this chunk (Y, Z: swizzled [k][32] tiles; SAME: Z is Y).
+template <int PP, bool SAME>
+__device__ __forceinline__ void oz_gram_add(double* sums, const double2* Y, const double2* Z, int p, int lane) {
+  using G = OzGramGeo<PP>;
+  static_assert(PP == 8 || PP == 16, "exact-slice Grams are built for p <= 16");
+  const int ey = oz_tile_colexp<PP>(Y, p, lane);
+  const int ez = SAME ? ey : oz_tile_colexp<PP>(Z, p, lane);
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < G::MT; ++mt) {
+    const int ma = 16 * mt + g, mb = ma + 8;
+    const int eba = __shfl_sync(0xffffffffu, ey, ma), ebb = __shfl_sync(0xffffffffu, ey, mb);
+    // A = Y'^T: rows m (columns of Y'), columns k (rows of the chunk)
+    unsigned A[OZ_NSL][2][4];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      unsigned long long F[8];
+      unsigned sg[8];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int r = 16 * ks + 2 * q + (c & 1) + 8 * (c >> 1);
+        const double va = oz_tile_val<PP>(Y, p, r, ma), vb = oz_tile_val<PP>(Y, p, r, mb);
+        F[2 * c] = oz_fixed(va, eba);
+        sg[2 * c] = (__double_as_longlong(va) < 0) ? 1u : 0u;
+        F[2 * c + 1] = oz_fixed(vb, ebb);
+        sg[2 * c + 1] = (__double_as_longlong(vb) < 0) ? 1u : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < OZ_NSL; ++t) {
+        const int shft = 56 - OZ_DB * (t + 1);
+        unsigned h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) h[e] = oz_bf16((unsigned)((F[e] >> shft) & 127ull), sg[e]);
+        A[t][ks][0] = h[0] | (h[2] << 16);
+        A[t][ks][1] = h[1] | (h[3] << 16);
+        A[t][ks][2] = h[4] | (h[6] << 16);
+        A[t][ks][3] = h[5] | (h[7] << 16);
+      }
+    }
+#pragma unroll 1
+    for (int nt = 0; nt < G::NT; ++nt) {
+      // B = Z': rows k (rows of the chunk), column n = 8 nt + g
+      const int n = 8 * nt + g;
+      const int ebn = __shfl_sync(0xffffffffu, ez, n);
+      uint2 Bf[OZ_NSL][2];
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        unsigned long long F[4];
+        unsigned sg[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int r = 16 * ks + 2 * q + (c & 1) + 8 * (c >> 1);
+          const double v = oz_tile_val<PP>(Z, p, r, n);
+          F[c] = oz_fixed(v, ebn);
+          sg[c] = (__double_as_longlong(v) < 0) ? 1u : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < OZ_NSL; ++t) {
+          const int shft = 56 - OZ_DB * (t + 1);
+          unsigned h[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) h[c] = oz_bf16((unsigned)((F[c] >> shft) & 127ull), sg[c]);
+          Bf[t][ks] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        }
+      }
+      float acc[OZ_NLEV][4];
+#pragma unroll
+      for (int l = 0; l < OZ_NLEV; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.f;
+#pragma unroll
+      for (int s = 1; s <= OZ_NSL; ++s) {
+#pragma unroll
+        for (int t = 1; t <= OZ_NSL; ++t) {
+          if (s + t > OZ_LMAX) continue;
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) oz_mma(acc[s + t - 2], A[s - 1][ks], Bf[t - 1][ks]);
+        }
+      }
+      // outputs (ma, 8nt+2q), (ma, 8nt+2q+1), (mb, 8nt+2q), (mb, 8nt+2q+1)
+      const int ec0 = __shfl_sync(0xffffffffu, ez, 8 * nt + 2 * q), ec1 = __shfl_sync(0xffffffffu, ez, 8 * nt + 2 * q + 1);
+      double* dst = sums + ((mt * G::NT + nt) * 4) * 32 + lane;
+#pragma unroll
+      for (int o = 0; o < 4; ++o) dst[o * 32] += oz_recombine(acc, o, o < 2 ? eba : ebb, (o & 1) ? ec1 : ec0);
+    }
+  }
+}
+
+// P[m][n] of one warp's sums (C-fragment order)
+template <int PP>
+__device__ __forceinline__ double oz_gram_at(const double* sums, int m, int n) {
+  using G = OzGramGeo<PP>;
+  const int mt = m >> 4, mr = m & 15, nt = n >> 3, nc = n & 7;
+  const int o = (mr >> 3) * 2 + (nc & 1), lane = (mr & 7) * 4 + (nc >> 1);
+  return sums[((mt * G::NT + nt) * 4 + o) * 32 + lane];
+}
+
+// The CTA's triangle (a <= b, row-major) of Y^H Z (HERM) or Y^T Z from every warp's sums,
+// summed over the warps in order; all threads call it after a CTA barrier.
+template <int PP, bool HERM>
+__device__ __forceinline__ void oz_gram_write(const double* sums_all, double2* __restrict__ out, int p, int nwarp) {
+  using G = OzGramGeo<PP>;
+  const int E = p * (p + 1) / 2;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    int a = 0, rem = e;
+    while (rem >= p - a) {
+      rem -= p - a;
+      ++a;
+    }
+    const int b = a + rem;
+    double re = 0.0, im = 0.0;
+    for (int w = 0; w < nwarp; ++w) {
+      const double* S = sums_all + w * G::ACC;
+      const double p11 = oz_gram_at<PP>(S, a, b), p22 = oz_gram_at<PP>(S, PP + a, PP + b);
+      const double p12 = oz_gram_at<PP>(S, a, PP + b), p21 = oz_gram_at<PP>(S, PP + a, b);
+      re += HERM ? p11 + p22 : p11 - p22;
+      im += HERM ? p12 - p21 : p12 + p21;
+    }
+    out[e] = make_double2(re, im);
+  }
+}
+
 }  // namespace blcoc

@@ -434,13 +434,22 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   Fac<PP, S> T{G::MATS_SMEM ? T_s : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
   GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
+  double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
+  if constexpr (OZ) {
+    for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
+  }
   double dummy0 = 0.0, dummy1 = 0.0;
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     gather_rows<PP, C, false>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
     load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
-    g.template add<false>((a.flag & F_UEXPL) ? tY : tW, tY, lane);
+    if constexpr (OZ) {
+      if (a.flag & F_UEXPL) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tY, tY, p, lane);
+      else oz_gram_add<PP, false>(zsums + warp * OzGramGeo<PP>::ACC, tW, tY, p, lane);
+    } else {
+      g.template add<false>((a.flag & F_UEXPL) ? tY : tW, tY, lane);
+    }
     if (applyT) {
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
@@ -454,7 +463,8 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+  if constexpr (OZ) oz_gram_write<PP, false>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
+  else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
 template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
@@ -500,6 +510,10 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   Fac<PP, S> AL{G::MATS_SMEM ? mA : reinterpret_cast<const C*>(a.mats + M_ALPHA * PMAX * PMAX), p};
   GramAcc<G::NTRI, S> g;
   g.init(G_HERM, p, lane);
+  double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
+  if constexpr (OZ) {
+    for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
+  }
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(tW, blk<C>(a.Q), r0, n, p, lane);
@@ -512,12 +526,14 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
       apply_full<PP, S, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
     }
     __syncwarp();
-    g.template add<true>(tW, tW, lane);
+    if constexpr (OZ) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tW, tW, p, lane);
+    else g.template add<true>(tW, tW, lane);
     store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+  if constexpr (OZ) oz_gram_write<PP, true>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
+  else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
 template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
@@ -733,7 +749,9 @@ __global__ void __launch_bounds__(256) k_axpy(const PassArgs a) {
 // ---------------------------------------------------------------------------------- launch
 enum PassKind { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_AXPY, K_NKIND };
 
-template <int PP, typename S>
+// OZ: the tensor-core variant, whose pass A and SpMM also keep every warp's running Gram
+// sums (OzGramGeo<PP>::ACC doubles) after the tiles.
+template <int PP, typename S, bool OZ = false>
 constexpr size_t pass_smem(int kind) {
   using G = Geo<PP, S>;
   const size_t esz = sizeof(typename Cx<S>::T);
@@ -748,6 +766,7 @@ constexpr size_t pass_smem(int kind) {
   const size_t red = (size_t)NWARP * tri_count(PP) * sizeof(double2);
   const bool has_gram = kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1;
   if (has_gram && s < mats + red) s = mats + red;
+  if (OZ && (kind == K_COCR_A || kind == K_SPMM_GRAM)) s += (size_t)NWARP * OzGramGeo<PP>::ACC * sizeof(double);
   return s;
 }
 
@@ -777,7 +796,7 @@ int pass_grid(int64_t n, int kind, int num_sms) {
   cudaGetDevice(&dev);
   int per_sm = (dev >= 0 && dev < 64) ? cache[dev][kind] : 0;
   if (per_sm == 0) {
-    const size_t smem = pass_smem<PP, S>(kind);
+    const size_t smem = pass_smem<PP, S, OZ>(kind);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<PP, S, OZ>(kind), NWARP * 32, smem) ==
             cudaSuccess &&
         per_sm > 0) {
@@ -796,10 +815,10 @@ int pass_grid(int64_t n, int kind, int num_sms) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <int PP, typename S, int KIND, void (*K)(const PassArgs)>
+template <int PP, typename S, int KIND, void (*K)(const PassArgs), bool OZ = false>
 void launch_pass(const PassArgs& a, cudaStream_t s) {
   if constexpr (KIND == K_AXPY) K<<<a.grid, 256, 0, s>>>(a);
-  else K<<<a.grid, NWARP * 32, pass_smem<PP, S>(KIND), s>>>(a);
+  else K<<<a.grid, NWARP * 32, pass_smem<PP, S, OZ>(KIND), s>>>(a);
 }
 
 template <int PP, typename S>
@@ -849,11 +868,11 @@ void prepare_pass_kernels_tc() {
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || done[dev]) return;
   cudaFuncSetAttribute(k_spmm_gram<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<PP, double>(K_SPMM_GRAM));
+                       (int)pass_smem<PP, double, true>(K_SPMM_GRAM));
   cudaFuncSetAttribute(k_cocr_passA<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<PP, double>(K_COCR_A));
+                       (int)pass_smem<PP, double, true>(K_COCR_A));
   cudaFuncSetAttribute(k_cocr_passC<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<PP, double>(K_COCR_C));
+                       (int)pass_smem<PP, double, true>(K_COCR_C));
   done[dev] = true;
 }
 
@@ -861,10 +880,10 @@ template <int PP>
 const KernelSet& kernel_set_tc() {
   static const KernelSet ks = {
       &launch_pass<PP, double, K_RESID, k_resid<PP, double>>,
-      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>>,
+      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>, true>,
       &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
-      &launch_pass<PP, double, K_COCR_A, k_cocr_passA<PP, double, true>>,
-      &launch_pass<PP, double, K_COCR_C, k_cocr_passC<PP, double, true>>,
+      &launch_pass<PP, double, K_COCR_A, k_cocr_passA<PP, double, true>, true>,
+      &launch_pass<PP, double, K_COCR_C, k_cocr_passC<PP, double, true>, true>,
       &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
