@@ -97,16 +97,25 @@ __device__ void gstore(double2* __restrict__ g, const double2* s, int p) {
 }
 
 // C = op(A) op(B), op = transpose (no conjugation) when the flag is set; C must not alias.
+// SA / SB: structure of op(A) / op(B) - 0 full, 1 upper triangular, 2 lower triangular -
+// whose zero half is skipped.  Even and odd k go to two accumulators as in the full
+// product, and the skipped terms are exact zeros, so the result is the full product's.
+template <int SA = 0, int SB = 0>
 __device__ void matmul(double2* C, const double2* A, bool tA, const double2* B, bool tB, int p) {
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e / p, j = e % p;
+    int k0 = 0, k1 = p;
+    if (SA == 1) k0 = max(k0, i);
+    if (SA == 2) k1 = min(k1, i + 1);
+    if (SB == 1) k1 = min(k1, j + 1);
+    if (SB == 2) k0 = max(k0, j);
     double2 acc0 = cz(), acc1 = cz();
-    int k = 0;
-    for (; k + 2 <= p; k += 2) {
+    int k = k0 & ~1;
+    for (; k + 2 <= k1; k += 2) {
       cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
       cmac(acc1, tA ? A[(k + 1) * LD + i] : A[i * LD + k + 1], tB ? B[j * LD + k + 1] : B[(k + 1) * LD + j]);
     }
-    if (k < p) cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
+    if (k < k1) cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
     C[i * LD + j] = make_double2(acc0.x + acc1.x, acc0.y + acc1.y);
   }
   __syncthreads();
@@ -221,6 +230,11 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
         const double v = __longlong_as_double((long long)best);
         ish[0] = bi;
         ish[1] = (bi < p && v > 0.0 && isfinite(v)) ? 1 : 0;
+        if (ish[1]) {   // reciprocal of the pivot, formed once for the whole CTA
+          const double2 r = crecip_fast(M[bi * LD + k]);
+          sh[2 * PMAX] = r.x;
+          sh[2 * PMAX + 1] = r.y;
+        }
       }
     }
     __syncthreads();
@@ -241,7 +255,7 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
       }
       __syncthreads();
     }
-    const double2 pinv = crecip_fast(M[k * LD + k]);
+    const double2 pinv = make_double2(sh[2 * PMAX], sh[2 * PMAX + 1]);
     for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) M[i * LD + k] = cmul(M[i * LD + k], pinv);
     __syncthreads();
     const int m = p - k - 1, w = m + nrhs;
@@ -341,8 +355,8 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     expand_tri(S.gs + 2 * E, S.m[3], p, false);
-    matmul(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
-    matmul(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
+    matmul<2, 0>(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
+    matmul<0, 1>(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
     gstore(slot(mats, M_H), S.m[5], p);
   }
 }
@@ -353,8 +367,8 @@ __device__ __noinline__ void d_small_cocr_H0(SmallShared& S, int p, const double
   sum_stage1(stage1, ncomp, S.gs);
   expand_tri(S.gs, S.m[0], p, false);
   gload(S.m[1], slot(mats, M_TINV), p);
-  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
-  matmul(S.m[3], S.m[2], false, S.m[1], false, p);
+  matmul<2, 0>(S.m[2], S.m[1], true, S.m[0], false, p);
+  matmul<0, 1>(S.m[3], S.m[2], false, S.m[1], false, p);
   gstore(slot(mats, M_H), S.m[3], p);
 }
 
@@ -393,7 +407,7 @@ __device__ __noinline__ void d_small_alpha(SmallShared& S, int p, const double* 
     return;
   }
   gstore(slot(mats, M_ALPHA), S.m[2], p);
-  matmul(S.m[3], S.m[2], false, S.m[0], false, p);
+  matmul<0, 1>(S.m[3], S.m[2], false, S.m[0], false, p);   // alpha' xi, xi upper triangular
   gstore(slot(mats, M_ALPHAXI), S.m[3], p);
   emit_oz(oz, OZ_ALPHA, S.m[2], p, S.colexp);
   emit_oz(oz, OZ_ALPHAXI, S.m[3], p, S.colexp);
@@ -442,7 +456,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   }
   tri_inv_upper(S.m[1], S.m[2], p, S.red);
   gload(S.m[3], slot(mats, M_XI), p);
-  matmul(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
+  matmul<1, 1>(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
   gstore(slot(mats, M_XI), S.m[4], p);
   gstore(slot(mats, M_TAU), S.m[1], p);
   gstore(slot(mats, M_TINV), S.m[2], p);
@@ -450,9 +464,9 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   if (method == 0) {
     const int E = tri_count(p);
     expand_tri(S.gs + 2 * E, S.m[0], p, false);       // W^T W
-    matmul(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
-    matmul(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
-    matmul(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
+    matmul<2, 0>(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
+    matmul<0, 1>(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
+    matmul<2, 0>(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
     gload(S.m[3], slot(mats, M_H), p);                // G_QQ (old)
     gstore(slot(mats, M_H), S.m[0], p);
     if (!lu_solve(S.m[3], S.m[4], p, p, S.red, S.ish)) {
@@ -469,10 +483,10 @@ __device__ __noinline__ void d_small_cocr_beta(SmallShared& S, int p, const doub
   sum_stage1(stage1, ncomp, S.gs);
   expand_tri(S.gs, S.m[0], p, false);
   gload(S.m[1], slot(mats, M_TINV), p);
-  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
-  matmul(S.m[3], S.m[2], false, S.m[1], false, p);   // H+
+  matmul<2, 0>(S.m[2], S.m[1], true, S.m[0], false, p);
+  matmul<0, 1>(S.m[3], S.m[2], false, S.m[1], false, p);   // H+
   gload(S.m[4], slot(mats, M_TAU), p);
-  matmul(S.m[5], S.m[4], true, S.m[3], false, p);    // tau^T H+
+  matmul<2, 0>(S.m[5], S.m[4], true, S.m[3], false, p);    // tau^T H+
   gload(S.m[0], slot(mats, M_H), p);
   gstore(slot(mats, M_H), S.m[3], p);
   if (!lu_solve(S.m[0], S.m[5], p, p, S.red, S.ish)) {
