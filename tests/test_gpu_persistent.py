@@ -145,3 +145,65 @@ def test_persistent_rejects_wide_blocks():
     with pytest.raises(blcoc.BlcocError):
         blcoc.solve_batched([h], [B], [X], persistent=True)
     h.close()
+
+
+def test_persistent_edge_cases_match_graph_form_bitwise():
+    """A zero right-hand side (stopped at setup), a system that reaches maxit, a one-system
+    batch, and 40 tiny systems (the ticket ring wraps around many times): every system
+    equals the graph-branch form and a separate solve bit for bit, with the same status."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    specs = [(900, 3, "zero"), (1200, 4, "ok"), (700, 2, "ok")]
+    systems = []
+    for i, (n, p, kind) in enumerate(specs):
+        A = P.random_complex_symmetric(n, 8, seed=600 + i, diag=3.0 + 0.6j, scale=0.25)
+        Bh = P.complex_normal(n, p, 700 + i) * (0.0 if kind == "zero" else 1.0)
+        systems.append((A, Bh))
+    hard = P.helmholtz2d_batch(1, seed=9, side_range=(60, 60), k_range=(20.0, 20.0))[0]
+    systems.append((hard.A, hard.B))                      # needs far more than 30 iterations
+    tiny = P.helmholtz2d_batch(40, seed=11, side_range=(6, 14), k_range=(2.0, 5.0))
+    systems += [(pr.A, pr.B) for pr in tiny]
+    maxit = 30
+
+    def run(form):
+        hs = [blcoc.Handle.from_csr(A) for A, _ in systems]
+        Bs = [to_dev(torch, Bh) for _, Bh in systems]
+        Xs = [torch.zeros_like(B) for B in Bs]
+        if form == "separate":
+            sts = [h.solve(B, X, tol=1e-10, maxit=maxit) for h, B, X in zip(hs, Bs, Xs)]
+            st = max(sts)
+        else:
+            st, _, _ = blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=maxit, autotune=False,
+                                           persistent=(form == "persistent"))
+        out = [(X.cpu().numpy(), h.info()) for X, h in zip(Xs, hs)]
+        for h in hs:
+            h.close()
+        return st, out
+
+    st_p, pers = run("persistent")
+    st_g, graph = run("graph")
+    _, sep = run("separate")
+    assert st_p == st_g == blcoc.BLCOC_NOT_CONVERGED          # the Helmholtz system hits maxit
+    assert not pers[0][0].any() and pers[0][1]["iters"] == 0   # B = 0: X = 0 at once
+    assert pers[3][1]["iters"] == maxit
+    for (Xp, ip), (Xg, ig), (Xs_, is_) in zip(pers, graph, sep):
+        assert ip["iters"] == ig["iters"] == is_["iters"]
+        assert np.array_equal(Xp, Xg) and np.array_equal(Xp, Xs_)
+        assert np.array_equal(ip["hist"], ig["hist"]) and np.array_equal(ip["hist"], is_["hist"])
+
+
+def test_persistent_single_system_equals_solve():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    pr = P.helmholtz2d_n1024_p4("cocr_rq")
+    h = blcoc.Handle.from_csr(pr.A)
+    B = to_dev(torch, pr.B)
+    X1 = torch.zeros_like(B)
+    assert h.solve(B, X1, tol=1e-10, maxit=500) == blcoc.BLCOC_OK
+    i1 = h.info()
+    X2 = torch.zeros_like(B)
+    st, _, msg = blcoc.solve_batched([h], [B], [X2], tol=1e-10, maxit=500, autotune=False, persistent=True)
+    assert st == blcoc.BLCOC_OK, msg
+    assert np.array_equal(X1.cpu().numpy(), X2.cpu().numpy())
+    assert h.info()["iters"] == i1["iters"]
+    h.close()
