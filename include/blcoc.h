@@ -224,6 +224,14 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  computes them with FP64 FMAs.
  *   "u_explicit_mixed": the same for the complex64 inner solves of BLCOC_COCR_RQ_MIXED
  *                  (default 1: the recurrence drifts quickly in single precision).
+ *   "qr_passes"  : rq methods: 1 (default) forms the thin QR of W (Sec. 2.2, Q^H Q = I)
+ *                  as a Cholesky QR: tau from the Gram W^H W of the pass that forms W,
+ *                  Q = W tau^{-1} applied lazily; its orthogonality error grows like
+ *                  cond(W)^2 eps.  2: CholQR2 - after every Cholesky QR (setup included)
+ *                  one more pass replaces W by Q1 = W tau1^{-1} and forms Q1^H Q1, a second
+ *                  Cholesky factor tau2 follows and tau = tau2 tau1 (error about cond(W)
+ *                  eps, like a Householder QR).  One extra read/write pass of W per
+ *                  iteration.  Not available in blcoc_solve_batched_persistent.
  *   "persistent_timeout_ms": blcoc_solve_batched_persistent (read from hs[0]): limit of
  *                  one wait of the kernel, in [1, 600000] ms (default 10000).
  *   "persistent_stall": blcoc_solve_batched_persistent (read from hs[0]), a test of the

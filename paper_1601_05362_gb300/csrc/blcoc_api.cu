@@ -50,11 +50,13 @@ __global__ void k_vals_to_c64(const double2* __restrict__ v, float2* __restrict_
 }
 
 // Names of the timed kernel kinds (index = PassKind of blcoc_rowpass.cuh).
-const char* const kKindNames[] = {"resid",      "spmm_gram",  "spmm_plain", "cocr_passA", "cocr_passC",
-                                  "cocg_pass1", "cocg_pass2", "reduce",     "small_setup", "small_H0",
-                                  "small_alpha", "small_chol", "small_beta", "small_trr",  "small_setup_inner"};
-constexpr int kNumKinds = 15;
+const char* const kKindNames[] = {"resid",       "spmm_gram",   "spmm_plain",  "cocr_passA",  "cocr_passC",
+                                  "cocg_pass1",  "cocg_pass2",  "reduce",      "small_setup", "small_H0",
+                                  "small_alpha", "small_chol",  "small_beta",  "small_trr",   "small_setup_inner",
+                                  "small_chol2", "small_chol2_setup", "qr2"};
+constexpr int kNumKinds = 18;
 constexpr int kKindReduce = 7, kKindSmall0 = 8;   // small kernel kind = kKindSmall0 + SmallKind
+constexpr int kKindQR2 = 17;
 
 struct Timer {
   int kind;
@@ -119,6 +121,7 @@ struct blcoc_ctx {
   uint2* ozbuf = nullptr;     // their factor fragments
   int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
   int u_explicit_mixed = 1;   // the same for the complex64 inner solves
+  int qr_passes = 1;          // 2: CholQR2 (one re-orthogonalising pass after every Cholesky QR)
   int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
   int persistent_stall = 0;   // persistent batch, test hook: no first work item is published
   int stat_persistent_graph = -1;   // last persistent batch: 1 graph replays, 0 direct launches
@@ -280,13 +283,13 @@ struct Solver {
     }
     return h->evpool[h->evnext++];
   }
-  void pass(LaunchFn f, int kind, int ne, int flag, double2* in = nullptr) {
+  void pass(LaunchFn f, int kind, int ne, int flag, double2* in = nullptr, int tkind = -1) {
     PassArgs a = base();
     if (in) a.W = in;   // spmm_gram gathers a.W
     a.ne = ne;
     a.flag = flag;
     a.grid = K->grid(h->n, kind, sms());
-    Timer t{kind, batch_iter, nullptr, nullptr};
+    Timer t{tkind >= 0 ? tkind : kind, batch_iter, nullptr, nullptr};
     if (timers) {
       t.e0 = next_event();
       t.e1 = next_event();
@@ -330,12 +333,21 @@ struct Solver {
   void small(SmallKind k, int ne) {
     Timer t;
     if (time_small) timed_begin(t, kKindSmall0 + (int)k);
-    launch_small(k, p, method + 16 * plain, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s, oz);
+    launch_small(k, p, method + 16 * plain + 32 * qr2, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s, oz);
     if (time_small) timed_end(t);
     ++launches;
   }
   // kinds must match PassKind in blcoc_rowpass.cuh
-  enum { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2 };
+  enum { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_AXPY, K_QR2 };
+  int qr2 = 0;   // CholQR2: after each Cholesky QR, W <- W T1 and a second factor
+  // CholQR2's second pass and factor (setup: the factor of R_0)
+  void second_qr(bool setup) {
+    if (!qr2 || plain) return;
+    const int E = tri_count(p);
+    pass(K->qr2, K_QR2, E, 0, nullptr, kKindQR2);
+    reduce(E, h->ctrl);
+    small(setup ? SK_CHOL2_SETUP : SK_CHOL2, E);
+  }
 
   // inner = 1: the right-hand side of this solve is the residual itself (refinement
   // step), so the stopping test is relative to ||R||_F instead of ||B||_F.
@@ -344,6 +356,7 @@ struct Solver {
     pass(K->resid, K_RESID, 2 * E + 1, method == BLCOC_COCG_RQ ? 2 : 0);
     reduce(2 * E + 1, h->ctrl);
     small(inner ? SK_SETUP_INNER : SK_SETUP, 2 * E + 1);
+    second_qr(true);
   }
   void setup_rest() {
     const int E = tri_count(p);
@@ -367,6 +380,7 @@ struct Solver {
       pass(K->cocr_passA, K_COCR_A, E, 0);
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
+      second_qr(false);
       pass(K->spmm_gram, K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (H+ of line 8)
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
@@ -391,6 +405,7 @@ struct Solver {
       pass(K->cocr_passA, K_COCR_A, E, 0);
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
+      second_qr(false);
       pass(K->spmm_gram, K_SPMM_GRAM, E, 1);
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
@@ -401,6 +416,7 @@ struct Solver {
       pass(K->cocg_pass1, K_COCG_1, 2 * E, 0);
       reduce(2 * E, h->ctrl);
       small(SK_CHOL, 2 * E);
+      second_qr(false);
       pass(K->cocg_pass2, K_COCG_2, 0, 0);
       pass(K->spmm_gram, K_SPMM_GRAM, E, 0, base().S);   // A S_{m+1}, gram S^T A S
       reduce(E, h->ctrl);
@@ -631,6 +647,12 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     (key[10] == 0 ? h->u_explicit : h->u_explicit_mixed) = (int)value;
     return BLCOC_OK;
   }
+  if (!strcmp(key, "qr_passes")) {
+    if (value != 1 && value != 2) return invalid(h, "qr_passes must be 1 or 2");
+    h->graph.reset();
+    h->qr_passes = (int)value;
+    return BLCOC_OK;
+  }
   if (!strcmp(key, "persistent_timeout_ms")) {
     if (value < 1 || value > 600000) return invalid(h, "persistent_timeout_ms must be in [1, 600000]");
     h->persistent_timeout_ms = (int)value;
@@ -820,8 +842,9 @@ blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, 
   sv.K->prepare();
   sv.use_c64_blocks();
   sv.uexpl = h->u_explicit_mixed != 0;
+  sv.qr2 = h->qr_passes == 2 ? 1 : 0;
   double2* D = reinterpret_cast<double2*>(h->w32[5]);
-  const int gkey = 100 + inner_method + (sv.uexpl ? 10 : 0);
+  const int gkey = 100 + inner_method + (sv.uexpl ? 10 : 0) + 80 * sv.qr2;
   std::vector<double> outer_hist;
   int total_inner = 0, outer = 0, done = 2, last_bd = 0;
   double bnorm = 0.0, relres = 0.0;
@@ -1174,6 +1197,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   sv.use_fp64_blocks();
   sv.plain = plain ? 1 : 0;
   sv.uexpl = !plain && h->u_explicit != 0;
+  sv.qr2 = h->qr_passes == 2 ? 1 : 0;
   Ctrl c0{};
   c0.maxit = maxit;
   c0.tol = tol;
@@ -1189,7 +1213,8 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   } else if (!h->h_ctrl->done) {
     sv.setup_rest();
     CK(h, cudaGetLastError());
-    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0), maxit);
+    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0) + 80 * sv.qr2,
+                        maxit);
     if (st != BLCOC_OK) return st;
   }
   // true residual of the returned iterate
@@ -1239,6 +1264,8 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     if (!hs[i] || hs[i]->dev != dev) return invalid(nullptr, "batched: handles must be non-NULL and on one device");
     if (p[i] < 1 || p[i] > BLCOC_MAX_P) return invalid(nullptr, "batched: p must be in [1, 32]");
     if (form == 1 && p[i] > PERSISTENT_PMAX) return invalid(nullptr, "batched (persistent): p must be in [1, 16]");
+    if (form == 1 && hs[i] && hs[i]->qr_passes != 1)
+      return invalid(nullptr, "batched (persistent): qr_passes = 2 is not supported; use blcoc_solve_batched");
     if (!B[i] || !X[i] || B[i] == X[i]) return invalid(nullptr, "batched: B[i], X[i] must be distinct device pointers");
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return invalid(nullptr, "batched: each system needs its own handle");
@@ -1266,6 +1293,7 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     sv.push_back(Solver{h, kernels_for(p[i], &PP), PP, p[i], (int)method, (const double2*)B[i], (double2*)X[i]});
     sv.back().K->prepare();
     sv.back().use_fp64_blocks();
+    sv.back().qr2 = h->qr_passes == 2 ? 1 : 0;
     Ctrl c0{};
     c0.maxit = maxit;
     c0.tol = tol;

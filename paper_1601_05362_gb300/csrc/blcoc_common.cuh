@@ -51,7 +51,7 @@ enum MatSlot {
   M_ALPHAXI,     // alpha'_m xi_m
   M_BETA,        // beta'_m
   M_H,           // cocr: H_m = Q_m^T V_m;  cocg: G_QQ = Q_m^T Q_m
-  M_G1,          // cocr: U^T U;  cocg: S^T A S
+  M_G1,          // CholQR2 with cocg: W^T W (R^T R at setup) kept for the second factor
   M_NSLOTS
 };
 
@@ -157,6 +157,7 @@ struct KernelSet {
   LaunchFn cocg_pass1;   // W <- Q - (AS) alpha'; X += S alpha'xi; grams W^H W, W^T W
   LaunchFn cocg_pass2;   // Q = W T (stored); S <- Q + S beta'
   LaunchFn axpy;         // X (FP64) += D (working precision), the refinement update
+  LaunchFn qr2;          // CholQR2 second pass: W <- W T (stored); gram W^H W
   int (*grid)(int64_t n, int kind, int num_sms);
   void (*prepare)();     // set the dynamic shared-memory limits (once per device)
 };

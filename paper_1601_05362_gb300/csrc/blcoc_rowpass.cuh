@@ -728,6 +728,42 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
   d_cocg_pass2<PP, S>(a, blockIdx.x, gridDim.x);
 }
 
+// CholQR2, second pass (the thin QR of Sec. 2.2 with one re-orthogonalisation): the
+// first Cholesky factor's T1 is applied to W in place (W <- Q1 = W T1, stored) and the
+// Gram Q1^H Q1 is formed for the second factor.  Partials: [Q1^H Q1 tri].
+template <int PP, typename S>
+__device__ __forceinline__ void d_qr2(const PassArgs& a, const int vblk, const int vgrid) {
+  using C = typename Cx<S>::T;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, S>;
+  C* mT = smem;
+  C* tiles = smem + mats_off<PP, S>(1);
+  C* tW = tiles + warp * G::TILE;
+  if constexpr (G::MATS_SMEM) {
+    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
+    __syncthreads();
+  }
+  Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
+  GramAcc<G::NTRI, S> g;
+  g.init(G_HERM, p, lane);
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
+    __syncwarp();
+    tri_apply_inplace<PP, S>(tW, T, p, lane);
+    __syncwarp();
+    g.template add<true>(tW, tW, lane);
+    store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+}
+template <int PP, typename S>
+__global__ void __launch_bounds__(NWARP * 32) k_qr2(const PassArgs a) {
+  d_qr2<PP, S>(a, blockIdx.x, gridDim.x);
+}
+
 // Refinement update of the mixed-precision form: X (FP64) += D (working precision, held
 // in a.V), elementwise over the n x p block.
 template <int PP, typename S>
@@ -747,7 +783,7 @@ __global__ void __launch_bounds__(256) k_axpy(const PassArgs a) {
 #undef BLCOC_PROLOGUE
 
 // ---------------------------------------------------------------------------------- launch
-enum PassKind { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_AXPY, K_NKIND };
+enum PassKind { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_AXPY, K_QR2, K_NKIND };
 
 // OZ: the tensor-core variant, whose pass A and SpMM also keep every warp's running Gram
 // sums (OzGramGeo<PP>::ACC doubles) after the tiles.
@@ -756,15 +792,16 @@ constexpr size_t pass_smem(int kind) {
   using G = Geo<PP, S>;
   const size_t esz = sizeof(typename Cx<S>::T);
   const size_t tile = (size_t)G::TILE * esz;
-  const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2, 0};
-  const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2, 0};
+  const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2, 0, 1};
+  const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2, 0, 1};
   if (kind == K_RESID) return (size_t)NWARP * PP * CHUNK * sizeof(double2);   // FP64 residual tile
   const size_t mats = (size_t)mats_off<PP, S>(nmats[kind]) * esz;
   size_t s = mats + (size_t)NWARP * ntiles[kind] * tile;
   // the CTA-level Gram reduction reuses the tile area: NWARP * E double2 (two Grams at most
   // are written one after the other, so one E-sized area suffices)
   const size_t red = (size_t)NWARP * tri_count(PP) * sizeof(double2);
-  const bool has_gram = kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1;
+  const bool has_gram =
+      kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1 || kind == K_QR2;
   if (has_gram && s < mats + red) s = mats + red;
   if (OZ && (kind == K_COCR_A || kind == K_SPMM_GRAM)) s += (size_t)NWARP * OzGramGeo<PP>::ACC * sizeof(double);
   return s;
@@ -781,6 +818,7 @@ const void* pass_kernel(int kind) {
     case K_COCR_C: return (const void*)k_cocr_passC<PP, S, OZ>;
     case K_COCG_1: return (const void*)k_cocg_pass1<PP, S>;
     case K_COCG_2: return (const void*)k_cocg_pass2<PP, S>;
+    case K_QR2: return (const void*)k_qr2<PP, S>;
     default: return nullptr;
   }
 }
@@ -840,6 +878,7 @@ void prepare_pass_kernels() {
                        (int)pass_smem<PP, S>(K_COCG_1));
   cudaFuncSetAttribute(k_cocg_pass2<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, S>(K_COCG_2));
+  cudaFuncSetAttribute(k_qr2<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP, S>(K_QR2));
   done[dev] = true;
 }
 
@@ -854,6 +893,7 @@ const KernelSet& kernel_set() {
       &launch_pass<PP, S, K_COCG_1, k_cocg_pass1<PP, S>>,
       &launch_pass<PP, S, K_COCG_2, k_cocg_pass2<PP, S>>,
       &launch_pass<PP, S, K_AXPY, k_axpy<PP, S>>,
+      &launch_pass<PP, S, K_QR2, k_qr2<PP, S>>,
       &pass_grid<PP, S, false>,
       &prepare_pass_kernels<PP, S>,
   };
@@ -887,6 +927,7 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
+      &launch_pass<PP, double, K_QR2, k_qr2<PP, double>>,
       &pass_grid<PP, double, true>,
       &prepare_pass_kernels_tc<PP>,
   };

@@ -34,9 +34,9 @@ __global__ void k_reduce_stage1(const double* __restrict__ partials, int nparts,
   SmallShared& S = *reinterpret_cast<SmallShared*>(small_raw);
 
 __global__ void k_small_setup(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                              int inner, int plain, uint2* oz) {
+                              int inner, int plain, uint2* oz, int qr2) {
   SMALL_PROLOGUE
-  d_small_setup(S, p, method, stage1, ncomp, mats, ctrl, inner, plain, oz);
+  d_small_setup(S, p, method, stage1, ncomp, mats, ctrl, inner, plain, oz, qr2);
 }
 
 __global__ void k_small_cocr_H0(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl) {
@@ -51,9 +51,15 @@ __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* m
 }
 
 __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                             int plain, uint2* oz) {
+                             int plain, uint2* oz, int qr2) {
   SMALL_PROLOGUE
-  d_small_chol(S, p, method, stage1, ncomp, mats, ctrl, plain, oz);
+  d_small_chol(S, p, method, stage1, ncomp, mats, ctrl, plain, oz, qr2);
+}
+
+__global__ void k_small_chol2(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
+                              int setup, uint2* oz) {
+  SMALL_PROLOGUE
+  d_small_chol2(S, p, method, stage1, ncomp, mats, ctrl, setup, oz);
 }
 
 __global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, uint2* oz) {
@@ -129,6 +135,7 @@ static void set_small_attrs() {
   cudaFuncSetAttribute(k_small_cocr_H0, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_chol2, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_cocr_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_trr, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   done[dev] = true;
@@ -146,15 +153,20 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
                   double* hist, cudaStream_t s, uint2* oz) {
   const size_t sm = small_smem();
   const int ncomp = 2 * ne;
-  const int m = method & 15, plain = (method >> 4) & 1;   // method: 0 cocg / 1 cocr, +16 plain form
+  // method: 0 cocg / 1 cocr, +16 plain form, +32 CholQR2
+  const int m = method & 15, plain = (method >> 4) & 1, qr2 = (method >> 5) & 1;
   switch (kind) {
-    case SK_SETUP: k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, plain, oz); break;
-    case SK_SETUP_INNER:
-      k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, plain, oz);
+    case SK_SETUP:
+      k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, plain, oz, qr2);
       break;
+    case SK_SETUP_INNER:
+      k_small_setup<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, plain, oz, qr2);
+      break;
+    case SK_CHOL2: k_small_chol2<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, oz); break;
+    case SK_CHOL2_SETUP: k_small_chol2<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, oz); break;
     case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
     case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz); break;
-    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz); break;
+    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2); break;
     case SK_COCR_BETA: k_small_cocr_beta<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, oz); break;
     case SK_TRR: k_small_trr<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, ctrl); break;
   }

@@ -310,7 +310,7 @@ __device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s
 // inner = 1 (refinement step): the stopping test is relative to ||R_0||_F, the norm of
 // this solve's right-hand side, which is the outer residual.
 __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                              int inner, int plain, uint2* oz) {
+                              int inner, int plain, uint2* oz, int qr2 = 0) {
   if (BLCOC_LD(&ctrl->done)) return;
   sum_stage1(stage1, ncomp, S.gs);
   const int E = tri_count(p);
@@ -355,6 +355,10 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     expand_tri(S.gs + 2 * E, S.m[3], p, false);
+    if (qr2) {   // G_QQ needs the final factor: the second stage forms it from R^T R
+      gstore(slot(mats, M_G1), S.m[3], p);
+      return;
+    }
     matmul<2, 0>(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
     matmul<0, 1>(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
     gstore(slot(mats, M_H), S.m[5], p);
@@ -420,7 +424,7 @@ __device__ __noinline__ void d_small_alpha(SmallShared& S, int p, const double* 
 // plain: no QR; record ||R_{m+1}||_F^2 (trace of the Hermitian Gram) and, for block COCG,
 // beta = (R_m^T R_m)^{-1} R_{m+1}^T R_{m+1}.
 __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                             int plain, uint2* oz) {
+                             int plain, uint2* oz, int qr2 = 0) {
   if (BLCOC_LD(&ctrl->done)) return;
   sum_stage1(stage1, ncomp, S.gs);
   if (plain) {
@@ -464,6 +468,10 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   if (method == 0) {
     const int E = tri_count(p);
     expand_tri(S.gs + 2 * E, S.m[0], p, false);       // W^T W
+    if (qr2) {   // G_QQ+ and beta' need the final factor: the second stage forms them
+      gstore(slot(mats, M_G1), S.m[0], p);
+      return;
+    }
     matmul<2, 0>(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
     matmul<0, 1>(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
     matmul<2, 0>(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
@@ -475,6 +483,58 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
     }
     gstore(slot(mats, M_BETA), S.m[4], p);
   }
+}
+
+// CholQR2, second factor (after the pass W <- Q1 = W T1, Gram Q1^H Q1): tau2, T2 with
+// tau2^H tau2 = Q1^H Q1; the QR factor becomes tau = tau2 tau1 and the passes that follow
+// apply T2 to the stored Q1.  Iteration: xi_{m+1} <- tau2 xi_{m+1} (the first stage applied
+// tau1).  Setup (setup = 1): xi_0 = tau.  cocg also forms G_QQ (setup) or G_QQ+ and beta'
+// (iteration) from W^T W with the whole factor T1 T2.
+__device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, const double* stage1, int ncomp,
+                                           double2* mats, Ctrl* ctrl, int setup, uint2* oz) {
+  if (BLCOC_LD(&ctrl->done)) return;
+  sum_stage1(stage1, ncomp, S.gs);
+  expand_tri(S.gs, S.m[0], p, true);                   // Q1^H Q1
+  if (!chol_upper(S.m[0], S.m[1], p, S.red)) {
+    if (threadIdx.x == 0) {
+      ctrl->done = 3;
+      ctrl->bd_code = setup ? 1 : 3;
+      if (!setup && method == 1) ctrl->iter -= 1;
+    }
+    return;
+  }
+  tri_inv_upper(S.m[1], S.m[2], p, S.red);            // T2
+  gload(S.m[3], slot(mats, setup ? M_XI : M_TAU), p);  // tau1
+  matmul<1, 1>(S.m[4], S.m[1], false, S.m[3], false, p);   // tau = tau2 tau1
+  if (setup) {
+    gstore(slot(mats, M_XI), S.m[4], p);
+  } else {
+    gstore(slot(mats, M_TAU), S.m[4], p);
+    gload(S.m[5], slot(mats, M_XI), p);
+    matmul<1, 1>(S.m[3], S.m[1], false, S.m[5], false, p);   // xi <- tau2 xi
+    gstore(slot(mats, M_XI), S.m[3], p);
+  }
+  if (method == 0) {
+    gload(S.m[5], slot(mats, M_TINV), p);                   // T1
+    matmul<1, 1>(S.m[3], S.m[5], false, S.m[2], false, p);   // T1 T2
+    gload(S.m[0], slot(mats, M_G1), p);                     // W^T W (R^T R at setup)
+    matmul<2, 0>(S.m[5], S.m[3], true, S.m[0], false, p);
+    matmul<0, 1>(S.m[0], S.m[5], false, S.m[3], false, p);  // (T1 T2)^T G (T1 T2)
+    if (setup) {
+      gstore(slot(mats, M_H), S.m[0], p);                   // G_QQ
+    } else {
+      matmul<2, 0>(S.m[5], S.m[4], true, S.m[0], false, p); // tau^T G_QQ+
+      gload(S.m[3], slot(mats, M_H), p);                    // G_QQ (old)
+      gstore(slot(mats, M_H), S.m[0], p);
+      if (!lu_solve(S.m[3], S.m[5], p, p, S.red, S.ish)) {
+        if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 4; }
+        return;
+      }
+      gstore(slot(mats, M_BETA), S.m[5], p);
+    }
+  }
+  gstore(slot(mats, M_TINV), S.m[2], p);
+  emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
 }
 
 // cocr after V_{m+1} (Algorithm 3, line 8): H+ = T^T (W^T A W) T, beta' = H^{-1} tau^T H+.

@@ -78,3 +78,22 @@ def test_batched_rejects_shared_handles():
         blcoc.solve_batched([hs[0], hs[0]], [Bs[0], Bs[0]], Xs[:1] * 2)
     for h in hs:
         h.close()
+
+
+def test_batched_cholqr2_equals_separate_solves_bitwise():
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    probs, hs, Bs = _batch(torch, 6)
+    for h in hs:
+        h.set_option("qr_passes", 2)
+    ref = _separate(torch, hs, Bs)
+    Xs = [torch.zeros_like(B) for B in Bs]
+    st, ms, msg = blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False)
+    assert st == blcoc.BLCOC_OK
+    for (Xr, ir), X, h in zip(ref, Xs, hs):
+        assert h.info()["iters"] == ir["iters"]
+        assert np.array_equal(X.cpu().numpy(), Xr)
+    with pytest.raises(blcoc.BlcocError):   # the persistent form runs single-pass Cholesky QR only
+        blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False, persistent=True)
+    for h in hs:
+        h.close()

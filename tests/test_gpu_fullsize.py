@@ -114,3 +114,24 @@ def test_fp64_tc_first_iterations_and_solve(problem):
     trr_cpu = O.true_relres(A, pr.B, X.cpu().numpy())
     assert abs(info["relres_true"] - trr_cpu) <= 1e-6 * trr_cpu
     assert trr_cpu <= 1e-7
+
+
+def test_cholqr2_first_iterations_match_oracle(problem):
+    """CholQR2 (qr_passes = 2) at the bench size: history for m <= 20 and X_5 against the
+    oracle."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    pr = problem
+    A = pr.A.to_scipy()
+    ref = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=20)
+    ref5 = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=5)
+    with blcoc.Handle.from_csr(pr.A) as h:
+        h.set_option("qr_passes", 2)
+        B = to_dev(torch, pr.B)
+        X = torch.zeros_like(B)
+        assert h.solve(B, X, tol=0.0, maxit=5) == blcoc.BLCOC_NOT_CONVERGED
+        assert rel(X.cpu().numpy(), ref5.X) < 1e-10
+        X.zero_()
+        assert h.solve(B, X, tol=0.0, maxit=20) == blcoc.BLCOC_NOT_CONVERGED
+        hist = np.asarray(h.info()["hist"])
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8

@@ -306,3 +306,60 @@ def test_fp64_tc_full_solve_helmholtz2d():
     m = min(21, len(ref.hist))
     assert np.max(np.abs(info["hist"][:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m])) < HIST_TOL
     assert info["relres_true"] <= 1e-9
+
+
+@pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
+@pytest.mark.parametrize("p", [1, 4, 7, 16])
+def test_cholqr2_option_matches_oracle(method, p):
+    """Option qr_passes = 2 (CholQR2: a second pass W <- W T1 and a second Cholesky factor
+    after every Cholesky QR, setup included) against the oracle's Householder QR."""
+    torch = need_gpu()
+    n = 1500 + 3 * p
+    A = P.random_complex_symmetric(n, 8, seed=100 + p, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(n, p, 200 + p)
+    X0 = 0.1 * P.complex_normal(n, p, 300 + p)
+    m = 12
+    f = O.bl_cocg_rq if method == "cocg_rq" else O.bl_cocr_rq
+    ref = f(A.to_scipy(), Bh, X0=X0, tol=0.0, maxit=m)
+    h = _handle(A)
+    h.set_option("qr_passes", 2)
+    B = to_dev(torch, Bh)
+    X = to_dev(torch, X0)
+    assert h.solve(B, X, method=method, tol=0.0, maxit=m) == 5, h.last_error()
+    info = h.info()
+    assert info["iters"] == m
+    assert np.max(np.abs(info["hist"] - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
+    assert rel(X.cpu().numpy(), ref.X) < X_TOL
+    xi = h.xi(p)
+    assert np.max(np.abs(xi - ref.xi)) / np.linalg.norm(ref.xi) < HIST_TOL
+    X.copy_(to_dev(torch, X0))
+    assert h.solve(B, X, method=method, tol=1e-10, maxit=500) == 0
+    assert h.info()["relres_true"] <= 1e-9
+    h.close()
+
+
+@pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
+def test_cholqr2_on_nearly_dependent_right_hand_sides(method):
+    """B with nearly dependent columns (condition ~2.6e6, Gram condition ~7e12).  The QR
+    factor xi_0 (maxit = 0) against the oracle's Householder factor: single-pass Cholesky QR
+    loses about cond^2 eps in the small diagonal entries, CholQR2 keeps about cond eps
+    (both forms give the same iterates X, which do not depend on the basis)."""
+    torch = need_gpu()
+    n, p = 2000, 6
+    A = P.random_complex_symmetric(n, 8, seed=31, diag=3.0 + 0.6j, scale=0.25)
+    b = P.complex_normal(n, 1, 32)
+    Bh = np.repeat(b, p, axis=1) + 1e-6 * P.complex_normal(n, p, 33)
+    assert np.linalg.cond(Bh) > 1e6
+    f = O.bl_cocg_rq if method == "cocg_rq" else O.bl_cocr_rq
+    ref = np.diag(f(A.to_scipy(), Bh, tol=0.0, maxit=0).xi)
+    errs = {}
+    for qr in (1, 2):
+        h = _handle(A)
+        h.set_option("qr_passes", qr)
+        B = to_dev(torch, Bh)
+        X = torch.zeros_like(B)
+        assert h.solve(B, X, method=method, tol=0.0, maxit=0) == 5
+        errs[qr] = float(np.max(np.abs(np.diag(h.xi(p)) - ref) / np.abs(ref)))
+        h.close()
+    assert errs[2] < 1e-8, errs
+    assert errs[1] > 100 * errs[2], errs
