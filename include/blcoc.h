@@ -240,7 +240,8 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *   "timing"     : 1 brackets every kernel of the iterations with CUDA events on
  *                  the internal stream (also inside the graph) and accumulates per-kernel
  *                  device time; 2 brackets only the row-pass kernels (less overhead:
- *                  two event records per pass); 0 (default) records nothing.
+ *                  two event records per pass); 3 only the dominant row pass (pass C of
+ *                  bl_cocr_rq, pass 1 of bl_cocg_rq); 0 (default) records nothing.
  * Returns BLCOC_ERR_INVALID_ARG for an unknown key or value.
  */
 blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);

@@ -290,13 +290,14 @@ struct Solver {
     a.flag = flag;
     a.grid = K->grid(h->n, kind, sms());
     Timer t{tkind >= 0 ? tkind : kind, batch_iter, nullptr, nullptr};
-    if (timers) {
+    const bool timed = timers && (time_only < 0 || kind == time_only);
+    if (timed) {
       t.e0 = next_event();
       t.e1 = next_event();
       record(t.e0);
     }
     f(a, h->s);
-    if (timers) {
+    if (timed) {
       record(t.e1);
       timers->push_back(t);
     }
@@ -319,6 +320,11 @@ struct Solver {
     }
   }
   bool time_small = true;   // with timers: also bracket the reductions and p x p stages
+  int time_only = -1;       // with timers: >= 0 brackets only the row passes of this kind
+  void set_timing_mode(int mode) {
+    time_small = mode == 1;
+    time_only = mode == 3 ? (method == BLCOC_COCR_RQ ? (int)K_COCR_C : (int)K_COCG_1) : -1;
+  }
   void reduce(int ne, const Ctrl* ctrl) {
     Timer t;
     if (time_small) timed_begin(t, kKindReduce);
@@ -393,9 +399,10 @@ struct Solver {
         a.flag = 4;                                      // gram U^T U
         a.grid = K->grid(h->n, K_SPMM_GRAM, sms());
         Timer t;
-        timed_begin(t, K_SPMM_GRAM);
+        const bool timed = time_only < 0;
+        if (timed) timed_begin(t, K_SPMM_GRAM);
         K->spmm_gram(a, h->s);
-        timed_end(t);
+        if (timed) timed_end(t);
         ++launches;
         last_grid = a.grid;
       }
@@ -609,7 +616,7 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     return BLCOC_OK;
   }
   if (!strcmp(key, "timing")) {
-    if (value < 0 || value > 2) return invalid(h, "timing must be 0, 1 or 2");
+    if (value < 0 || value > 3) return invalid(h, "timing must be 0, 1, 2 or 3");
     if (h->timing != (int)value) h->graph.reset();
     h->timing = (int)value;
     return BLCOC_OK;
@@ -745,7 +752,7 @@ blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
       CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
       const int before = sv.launches;
       sv.timers = h->timing ? &g.timers : nullptr;
-      sv.time_small = h->timing == 1;
+      sv.set_timing_mode(h->timing);
       sv.capturing = true;
       for (int i = 0; i < batch; ++i) {
         sv.batch_iter = i;
@@ -784,7 +791,7 @@ blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
       if (h->timing) {
         h->evnext = 0;
         sv.timers = &direct_timers;
-        sv.time_small = h->timing == 1;
+        sv.set_timing_mode(h->timing);
       }
       for (int i = 0; i < batch; ++i) {
         sv.batch_iter = i;
