@@ -95,13 +95,21 @@ def algorithmic(pr):
 ROWPASS_SOURCES = ("blcoc_common.cuh", "blcoc_rowpass.cuh", "kset_p16.cu")
 
 
+def code_of(text):
+    """C/C++ source without comments and blank lines (what the compiler sees of the kernels)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_05362_gb300", "csrc")
     for fn in ROWPASS_SOURCES:
-        with open(os.path.join(csrc, fn), "rb") as f:
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
             h.update(fn.encode())
-            h.update(f.read())
+            h.update(code_of(f.read()).encode())
     return h.hexdigest()[:16]
 
 

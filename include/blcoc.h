@@ -94,7 +94,8 @@ blcoc_status blcoc_create(blcoc_handle* out, int64_t n, int64_t nnz, const int32
  *   X     : n x p, on entry the initial guess X_0, on exit the last iterate.
  *   p     : 1 <= p <= BLCOC_MAX_P.
  *   tol   : stop at the top of iteration m when ||xi_m||_F / ||B||_F <= tol
- *           (Algorithms 2-3, line 3); tol >= 0 (tol = 0 runs exactly maxit iterations).
+ *           (the test at the top of each iteration of Algorithms 2-3); tol >= 0 (tol = 0
+ *           runs exactly maxit iterations).
  *   maxit : maximum number of iterations, maxit >= 0.
  * B and X may be device pointers or host pointers (pageable or pinned); host data is
  * copied through handle-owned device buffers.  B must not alias X.

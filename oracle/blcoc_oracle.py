@@ -33,7 +33,7 @@ sides"):
   - the QR factor is normalised so that ``diag(xi)`` is real and non-negative (MATLAB's
     ``qr(W,0)`` leaves a diagonal unitary freedom that the iterates do not depend on);
   - stopping rule: ``||xi_m||_F / ||B||_F <= tol`` tested before iteration m; the
-    returned iteration count is m (Algorithms 2-3, line 3).
+    returned iteration count is m (the test at the top of each iteration of Algorithms 2-3).
 
 Every public solver returns a :class:`Result`.  ``hist[m]`` is the recursive relative
 residual at the top of iteration m (``||xi_m||_F/||B||_F`` for the rq forms,
@@ -137,8 +137,8 @@ def bl_cocg_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
     maxit = n if maxit is None else maxit
     X = _x0(B, X0)
     nb = fro(B)
-    Q, xi = thin_qr(B - A @ X)                 # line 1: Q_0 xi_0 = B - A X_0
-    S = Q.copy()                               # line 2: S_0 = Q_0
+    Q, xi = thin_qr(B - A @ X)                 # Q_0 xi_0 = B - A X_0
+    S = Q.copy()                               # S_0 = Q_0
     hist, rec = [], {"Q": [], "S": [], "X": [], "xi": [], "AS": []}
     status, m = NOT_CONVERGED, 0
     if rank_deficient(xi) and fro(xi) > 0:
@@ -148,7 +148,7 @@ def bl_cocg_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
         hist.append(res)
         if record:
             rec["Q"].append(Q.copy()); rec["S"].append(S.copy()); rec["X"].append(X.copy()); rec["xi"].append(xi.copy())
-        if res <= tol:                         # line 3: stop when ||xi_m||_F/||B||_F <= eps
+        if res <= tol:                         # stop when ||xi_m||_F/||B||_F <= eps
             status = CONVERGED
             break
         if m == maxit:
@@ -157,22 +157,22 @@ def bl_cocg_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
         if record:
             rec["AS"].append(AS.copy())
         try:
-            alpha = small_solve(bt(S, AS), bt(Q, Q))      # line 4: (S^T A S) alpha' = Q^T Q
+            alpha = small_solve(bt(S, AS), bt(Q, Q))      # (S^T A S) alpha' = Q^T Q
         except Breakdown:
             status = BREAKDOWN
             break
-        X = X + S @ (alpha @ xi)                          # line 5: X += S alpha' xi
-        Qn, tau = thin_qr(Q - AS @ alpha)                 # line 6: Q_{m+1} tau_{m+1} = Q_m - A S_m alpha'
+        X = X + S @ (alpha @ xi)                          # X += S alpha' xi
+        Qn, tau = thin_qr(Q - AS @ alpha)                 # Q_{m+1} tau_{m+1} = Q_m - A S_m alpha'
         if rank_deficient(tau):
             status, m = BREAKDOWN, m + 1
             break
-        xi = tau @ xi                                     #         xi_{m+1} = tau_{m+1} xi_m
+        xi = tau @ xi                                     # xi_{m+1} = tau_{m+1} xi_m
         try:
-            beta = small_solve(bt(Q, Q), tau.T @ bt(Qn, Qn))  # line 7: (Q_m^T Q_m) beta' = tau^T Q^T Q
+            beta = small_solve(bt(Q, Q), tau.T @ bt(Qn, Qn))  # (Q_m^T Q_m) beta' = tau^T Q^T Q
         except Breakdown:
             status, m = BREAKDOWN, m + 1
             break
-        S = Qn + S @ beta                                 # line 8: S_{m+1} = Q_{m+1} + S_m beta'
+        S = Qn + S @ beta                                 # S_{m+1} = Q_{m+1} + S_m beta'
         Q = Qn
     return Result(X=X, hist=hist, iters=m, status=status, xi=xi, record=rec if record else {})
 
@@ -180,11 +180,11 @@ def bl_cocg_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
 def bl_cocr_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False, alpha_rhs="QV", u_explicit=False) -> Result:
     """Block COCR with residual orthonormalization, Algorithm 3 (Sec. 2.2).
 
-    ``alpha_rhs`` selects the right-hand side of the alpha' system (line 4): ``"QV"``
+    ``alpha_rhs`` selects the right-hand side of the alpha' system: ``"QV"``
     (``Q_m^T V_m``, derived from Algorithm 1, default) or ``"QU"`` (``Q_m^T U_m``, as
-    printed).  ``u_explicit`` replaces line 10's recurrence ``U_{m+1} = V_{m+1} + U_m
-    beta'_m`` by the product ``U_{m+1} = A S_{m+1}`` it stands for (Sec. 2.1 introduces
-    the recurrence only to save that product)."""
+    printed).  ``u_explicit`` replaces the recurrence ``U_{m+1} = V_{m+1} + U_m beta'_m``
+    by the product ``U_{m+1} = A S_{m+1}`` it stands for (Sec. 2.1 introduces the
+    recurrence only to save that product)."""
     if alpha_rhs not in ("QV", "QU"):
         raise ValueError("alpha_rhs must be 'QV' or 'QU'")
     B = np.asarray(B, dtype=np.complex128)
@@ -192,8 +192,8 @@ def bl_cocr_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False, alpha_rhs="QV
     maxit = n if maxit is None else maxit
     X = _x0(B, X0)
     nb = fro(B)
-    Q, xi = thin_qr(B - A @ X)                 # line 1
-    S = Q.copy()                               # line 2: S_0 = Q_0, U_0 = V_0 = A Q_0
+    Q, xi = thin_qr(B - A @ X)                 # Q_0 xi_0 = B - A X_0
+    S = Q.copy()                               # S_0 = Q_0, U_0 = V_0 = A Q_0
     V = A @ Q
     U = V.copy()
     hist, rec = [], {"Q": [], "S": [], "U": [], "V": [], "X": [], "xi": []}
@@ -213,24 +213,24 @@ def bl_cocr_rq(A, B, X0=None, tol=1e-10, maxit=None, record=False, alpha_rhs="QV
             break
         try:
             rhs = bt(Q, V) if alpha_rhs == "QV" else bt(Q, U)
-            alpha = small_solve(bt(U, U), rhs)            # line 4: (U^T U) alpha' = Q^T V
+            alpha = small_solve(bt(U, U), rhs)            # (U^T U) alpha' = Q^T V
         except Breakdown:
             status = BREAKDOWN
             break
-        X = X + S @ (alpha @ xi)                          # line 5 (read as X += S alpha' xi)
-        Qn, tau = thin_qr(Q - U @ alpha)                  # line 6
+        X = X + S @ (alpha @ xi)                          # X += S alpha' xi (the reading of the X update)
+        Qn, tau = thin_qr(Q - U @ alpha)                  # Q_{m+1} tau_{m+1} = Q_m - U_m alpha'
         if rank_deficient(tau):
             status, m = BREAKDOWN, m + 1
             break
         xi = tau @ xi
-        Vn = A @ Qn                                       # line 7: V_{m+1} = A Q_{m+1}
+        Vn = A @ Qn                                       # V_{m+1} = A Q_{m+1}
         try:
-            beta = small_solve(bt(Q, V), tau.T @ bt(Qn, Vn))  # line 8: (Q^T V) beta' = tau^T Q^T V
+            beta = small_solve(bt(Q, V), tau.T @ bt(Qn, Vn))  # (Q^T V) beta' = tau^T Q^T V
         except Breakdown:
             status, m = BREAKDOWN, m + 1
             break
-        S = Qn + S @ beta                                 # line 9
-        U = (A @ S) if u_explicit else (Vn + U @ beta)    # line 10
+        S = Qn + S @ beta                                 # S_{m+1} = Q_{m+1} + S_m beta'
+        U = (A @ S) if u_explicit else (Vn + U @ beta)    # U_{m+1} = V_{m+1} + U_m beta'
         Q, V = Qn, Vn
     return Result(X=X, hist=hist, iters=m, status=status, xi=xi, record=rec if record else {})
 
@@ -244,8 +244,8 @@ def bl_cocr(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
     maxit = n if maxit is None else maxit
     X = _x0(B, X0)
     nb = fro(B)
-    R = B - A @ X                               # line 1
-    P = R.copy()                                # line 2: P_0 = R_0, U_0 = V_0 = A R_0
+    R = B - A @ X                               # R_0 = B - A X_0
+    P = R.copy()                                # P_0 = R_0, U_0 = V_0 = A R_0
     V = A @ R
     U = V.copy()
     hist, rec = [], {"R": [], "P": [], "X": []}
@@ -260,13 +260,13 @@ def bl_cocr(A, B, X0=None, tol=1e-10, maxit=None, record=False) -> Result:
             break
         if m == maxit:
             break
-        alpha = small_solve(bt(U, U), bt(R, V))       # line 4
-        X = X + P @ alpha                             # line 5
-        Rn = R - U @ alpha                            # line 6
+        alpha = small_solve(bt(U, U), bt(R, V))       # (U^T U) alpha = R^T V
+        X = X + P @ alpha                             # X += P alpha
+        Rn = R - U @ alpha                            # R_{m+1} = R_m - U_m alpha
         Vn = A @ Rn
-        beta = small_solve(bt(R, V), bt(Rn, Vn))      # line 7
-        P = Rn + P @ beta                             # line 8
-        U = Vn + U @ beta                             # line 9
+        beta = small_solve(bt(R, V), bt(Rn, Vn))      # (R_m^T V_m) beta = R_{m+1}^T V_{m+1}
+        P = Rn + P @ beta                             # P_{m+1} = R_{m+1} + P_m beta
+        U = Vn + U @ beta                             # U_{m+1} = V_{m+1} + U_m beta
         R, V = Rn, Vn
     return Result(X=X, hist=hist, iters=m, status=status, record=rec if record else {})
 

@@ -1,4 +1,4 @@
-// C ABI of libblcoc.so and the host-side solve driver (see include/blcoc.h).
+// C ABI of libblcoc.so and the host-side solve loop (see include/blcoc.h).
 //
 // One solve = a setup sequence (residual, QR, first products) followed by batches of
 // iterations queued on an internal stream, optionally replayed as a CUDA graph.  The
@@ -225,7 +225,7 @@ blcoc_status ensure_ws(blcoc_ctx* h, int p) {
 
 }  // namespace
 
-// ------------------------------------------------------------------------------ driver
+// ------------------------------------------------------------------------------ solve loop
 namespace {
 
 struct Solver {
@@ -387,7 +387,7 @@ struct Solver {
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
       second_qr(false);
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (H+ of line 8)
+      pass(K->spmm_gram, K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (for H+ of the beta' step)
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
       pass(K->cocr_passC, K_COCR_C, 0, 4);               // Q, X, S (no U recurrence)
@@ -836,7 +836,7 @@ blcoc_status finish_solve(blcoc_ctx* h, Solver& sv, void* X, bool hostX, size_t 
   return BLCOC_OK;
 }
 
-// Mixed precision (SURVEY form f2): iterative refinement whose residual R = B - A X, the
+// Mixed precision: iterative refinement whose residual R = B - A X, the
 // p x p solves and the Cholesky QR are FP64, and whose inner correction solve A D = R
 // (bl_cocr_rq or bl_cocg_rq) runs its SpMM, Grams and block updates in complex64.
 blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, bool hostX, int p, int inner_method,

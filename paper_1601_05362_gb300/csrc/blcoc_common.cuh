@@ -1,5 +1,5 @@
 // Shared device-side definitions of libblcoc: control block, small-matrix slots,
-// complex FP64 arithmetic, and the launch-table type the host driver dispatches on.
+// complex FP64 arithmetic, and the launch-table type the host code dispatches on.
 #pragma once
 
 #include <cuda_runtime.h>

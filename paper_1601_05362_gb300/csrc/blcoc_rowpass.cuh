@@ -365,7 +365,7 @@ __device__ __forceinline__ const typename Cx<S>::T* vals_of(const CsrDev& A) {
   else return A.vaf;
 }
 
-// R = B - A X in FP64 (Sec. 3 residual, setup line 1 of Algorithms 2-3); R is written in
+// R = B - A X in FP64 (Sec. 3 residual, the setup of Algorithms 2-3); R is written in
 // the working precision S.  flag&1: norms only; flag&2: also R^T R (cocg).
 // Partials: [R^H R tri][R^T R tri][sum|B|^2, sum|R|^2]
 template <int PP, typename S>
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_spmm_plain(const PassArgs a) {
   d_spmm_plain<PP, S>(a, blockIdx.x, gridDim.x);
 }
 
-// bl_cocr_rq pass A (Algorithm 3, line 6 before the QR): W_{m+1} = Q_m - U_m alpha'_m
+// bl_cocr_rq pass A (Algorithm 3, the new residual block before its QR): W_{m+1} = Q_m - U_m alpha'_m
 // (Q_m stored by the previous pass C); gram W^H W for the Cholesky QR.
 template <int PP, typename S, bool OZ = false>
 __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, const int vgrid) {
@@ -540,11 +540,11 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
   d_cocr_passA<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 
-// bl_cocr_rq pass C (Algorithm 3, lines 5, 9, 10) with Q_{m+1} = W_{m+1} T_{m+1} (stored
+// bl_cocr_rq pass C (Algorithm 3, the X, S and U updates) with Q_{m+1} = W_{m+1} T_{m+1} (stored
 // for the next pass A):
 //   X_{m+1} = X_m + S_m (alpha'_m xi_m);  S_{m+1} = Q_{m+1} + S_m beta'_m;
 //   U_{m+1} = V_{m+1} + U_m beta'_m;  gram U^T U (next alpha').
-// flag=1 (setup, line 2): S_0 = Q_0, U_0 = V_0, X untouched.  flag&F_UEXPL: no U update
+// flag=1 (setup): S_0 = Q_0, U_0 = V_0, X untouched.  flag&F_UEXPL: no U update
 // and no gram (U_{m+1} = A S_{m+1} is formed by the SpMM that follows).
 template <int PP, typename S, bool OZ = false>
 __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, const int vgrid) {
@@ -636,9 +636,10 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   d_cocr_passC<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 
-// bl_cocg_rq pass 1 (Algorithm 2, lines 5-6), Q_m stored by the previous pass 2:
+// bl_cocg_rq pass 1 (Algorithm 2, the X update and the new residual block), Q_m stored by
+// the previous pass 2:
 //   W_{m+1} = Q_m - (A S_m) alpha'_m;  X_{m+1} = X_m + S_m (alpha'_m xi_m);
-//   grams W^H W (QR) and W^T W (Q^T Q of line 7).  Partials: [W^H W tri][W^T W tri].
+//   grams W^H W (QR) and W^T W (Q^T Q of the beta' step).  Partials: [W^H W tri][W^T W tri].
 template <int PP, typename S>
 __device__ __forceinline__ void d_cocg_pass1(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
@@ -688,8 +689,8 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
   d_cocg_pass1<PP, S>(a, blockIdx.x, gridDim.x);
 }
 
-// bl_cocg_rq pass 2 (Algorithm 2, line 8): Q_{m+1} = W_{m+1} T_{m+1} (stored for the next
-// pass 1), S_{m+1} = Q_{m+1} + S_m beta'_m.  flag=1 (setup, line 2): S_0 = Q_0 = W_0 T_0.
+// bl_cocg_rq pass 2 (Algorithm 2, the S update): Q_{m+1} = W_{m+1} T_{m+1} (stored for the next
+// pass 1), S_{m+1} = Q_{m+1} + S_m beta'_m.  flag=1 (setup): S_0 = Q_0 = W_0 T_0.
 template <int PP, typename S>
 __device__ __forceinline__ void d_cocg_pass2(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;

@@ -376,7 +376,8 @@ __device__ __noinline__ void d_small_cocr_H0(SmallShared& S, int p, const double
   gstore(slot(mats, M_H), S.m[3], p);
 }
 
-// Top of iteration m (Algorithms 2-3, lines 3-4): record ||xi_m||_F/||B||_F, stop if
+// Top of iteration m (Algorithms 2-3, the stopping test and the alpha' step): record
+// ||xi_m||_F/||B||_F, stop if
 // <= tol or m = maxit; else alpha'_m = G1^{-1} RHS with G1 = U^T U (cocr) or S^T A S
 // (cocg) and RHS = Q^T V (cocr) or Q^T Q (cocg); also alpha'_m xi_m.
 // plain: the stopping test uses ||R_m||_F (Algorithm 1) recorded by the previous stage.
@@ -418,8 +419,8 @@ __device__ __noinline__ void d_small_alpha(SmallShared& S, int p, const double* 
   if (threadIdx.x == 0) ctrl->iter = m + 1;
 }
 
-// After W_{m+1} (Algorithms 2-3, line 6): Cholesky QR tau, T = tau^{-1},
-// xi_{m+1} = tau xi_m.  cocg also does line 7: G_QQ+ = T^T (W^T W) T and
+// After W_{m+1} (Algorithms 2-3, the QR of the new residual block): Cholesky QR tau, T = tau^{-1},
+// xi_{m+1} = tau xi_m.  cocg also does the beta' step: G_QQ+ = T^T (W^T W) T and
 // beta' = G_QQ^{-1} tau^T G_QQ+.
 // plain: no QR; record ||R_{m+1}||_F^2 (trace of the Hermitian Gram) and, for block COCG,
 // beta = (R_m^T R_m)^{-1} R_{m+1}^T R_{m+1}.
@@ -537,7 +538,7 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
 }
 
-// cocr after V_{m+1} (Algorithm 3, line 8): H+ = T^T (W^T A W) T, beta' = H^{-1} tau^T H+.
+// cocr after V_{m+1} (Algorithm 3, the beta' step): H+ = T^T (W^T A W) T, beta' = H^{-1} tau^T H+.
 __device__ __noinline__ void d_small_cocr_beta(SmallShared& S, int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, uint2* oz) {
   if (BLCOC_LD(&ctrl->done)) return;
   sum_stage1(stage1, ncomp, S.gs);

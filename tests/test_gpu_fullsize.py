@@ -4,7 +4,7 @@ bl_cocr_rq in the launch configuration bench.py times (CUDA graph, poll 16).
 * the first iterations against the oracle run here: history <= 1e-8 for m <= 20;
   X_5 <= 1e-10; X_20 within 10x the oracle's own sensitivity to a rounding-level (1e-16)
   perturbation of B (about 7.5e-9 at this size: the iterates of this indefinite problem
-  amplify rounding differences, so the benchmark spec's 1e-10 on X holds early but not at m = 20
+  amplify rounding differences, so a 1e-10 bound on X holds early but not at m = 20
   for any two FP64 implementations);
 * the full solve against properties that hold at any size and against the oracle's own
   full solve stored in tests/golden/helmholtz3d_n262144_p16.json (written by

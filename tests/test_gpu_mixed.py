@@ -1,7 +1,7 @@
 """Mixed-precision form (iterative refinement around bl_cocr_rq / bl_cocg_rq with
 complex64 inner solves; FP64 residual, p x p solves and QR).
 
-The method is judged on what it promises: the FP64 true relative residual
+The tests check what the method promises: the FP64 true relative residual
 ||B - A X||_F/||B||_F recomputed here on the CPU reaches the tolerance, and the solution
 agrees with a dense LU solve (small, well-conditioned cases) and with the oracle's FP64
 solution; at n = 262,144 on the 27-point random complex symmetric family it reaches a
