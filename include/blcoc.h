@@ -120,6 +120,8 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
  * B[i], X[i]: device pointers.  ms_per_iter_out (may be NULL): device time per
  * system-iteration over the whole batch.  Per-system results: blcoc_get_info(hs[i]).
  * Returns BLCOC_OK if every system converged, else the first non-OK status.
+ * Each system runs with its own handle's options (fp64_tc, u_explicit, qr_passes), as
+ * blcoc_solve would.
  * The paper solves one system at a time; batching many is this library's addition.
  */
 blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
@@ -128,7 +130,8 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
 
 /*
  * blcoc_solve_batched_persistent - the same batch (arguments, results and statuses as
- * blcoc_solve_batched; p[i] <= 16, rq methods) with every iteration of every system in
+ * blcoc_solve_batched; p[i] <= 16, rq methods, handles without the options qr_passes = 2,
+ * fp64_tc and u_explicit) with every iteration of every system in
  * ONE persistent kernel launch.  An iteration of Algorithm 2 or 3 (Sec. 2.2) is a chain
  * of stages per system (row passes, their reductions, the p x p stages); the items of a
  * stage (a row pass's 32-row chunk groups, the reduction slices, one p x p solve) wait in

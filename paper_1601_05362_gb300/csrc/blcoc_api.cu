@@ -1271,8 +1271,10 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     if (!hs[i] || hs[i]->dev != dev) return invalid(nullptr, "batched: handles must be non-NULL and on one device");
     if (p[i] < 1 || p[i] > BLCOC_MAX_P) return invalid(nullptr, "batched: p must be in [1, 32]");
     if (form == 1 && p[i] > PERSISTENT_PMAX) return invalid(nullptr, "batched (persistent): p must be in [1, 16]");
-    if (form == 1 && hs[i] && hs[i]->qr_passes != 1)
-      return invalid(nullptr, "batched (persistent): qr_passes = 2 is not supported; use blcoc_solve_batched");
+    if (form == 1 && hs[i] && (hs[i]->qr_passes != 1 || hs[i]->fp64_tc || hs[i]->u_explicit))
+      return invalid(nullptr,
+                     "batched (persistent): qr_passes = 2, fp64_tc and u_explicit are not supported; use "
+                     "blcoc_solve_batched");
     if (!B[i] || !X[i] || B[i] == X[i]) return invalid(nullptr, "batched: B[i], X[i] must be distinct device pointers");
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return invalid(nullptr, "batched: each system needs its own handle");
@@ -1298,9 +1300,16 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
     int PP = 0;
     sv.push_back(Solver{h, kernels_for(p[i], &PP), PP, p[i], (int)method, (const double2*)B[i], (double2*)X[i]});
+    // per-system options, as in blcoc_solve: tensor-core block updates, explicit U, CholQR2
+    if (form == 0 && h->fp64_tc && method == BLCOC_COCR_RQ && (PP == 8 || PP == 16)) {
+      if (!h->ozbuf) CK(h, cudaMalloc(&h->ozbuf, (size_t)OZ_NSLOTS * OZ_SLOT_U2 * sizeof(uint2)));
+      sv.back().K = PP == 8 ? &kernel_set_tc<8>() : &kernel_set_tc<16>();
+      sv.back().oz = h->ozbuf;
+    }
     sv.back().K->prepare();
     sv.back().use_fp64_blocks();
     sv.back().qr2 = h->qr_passes == 2 ? 1 : 0;
+    sv.back().uexpl = method == BLCOC_COCR_RQ && h->u_explicit != 0;
     Ctrl c0{};
     c0.maxit = maxit;
     c0.tol = tol;

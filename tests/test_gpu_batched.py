@@ -97,3 +97,28 @@ def test_batched_cholqr2_equals_separate_solves_bitwise():
         blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False, persistent=True)
     for h in hs:
         h.close()
+
+
+def test_batched_honours_tensor_core_and_explicit_u_options():
+    """Per-handle options (fp64_tc, u_explicit) apply to that system in a batch exactly as
+    in a separate blcoc_solve: the batch equals separate solves bit for bit."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    probs = P.helmholtz2d_batch(8, seed=7, side_range=(20, 60), k_range=(3.0, 9.0), p_choices=(4, 8, 16))
+    hs = [blcoc.Handle.from_csr(pr.A) for pr in probs]
+    Bs = [to_dev(torch, pr.B) for pr in probs]
+    for i, h in enumerate(hs):
+        h.set_option("fp64_tc", 1)
+        h.set_option("u_explicit", i % 2)
+    ref = _separate(torch, hs, Bs)
+    Xs = [torch.zeros_like(B) for B in Bs]
+    st, ms, msg = blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False)
+    assert st == blcoc.BLCOC_OK
+    for (Xr, ir), X, h in zip(ref, Xs, hs):
+        assert h.info()["iters"] == ir["iters"]
+        assert np.array_equal(X.cpu().numpy(), Xr)
+        assert h.info()["relres_true"] <= 1e-9
+    with pytest.raises(blcoc.BlcocError):
+        blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False, persistent=True)
+    for h in hs:
+        h.close()
