@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/blcoc.h"
 #include "blcoc_common.cuh"
 #include "blcoc_ozaki.cuh"
@@ -62,6 +64,14 @@ struct Timer {
   int kind;
   int iter;   // iteration index within the batch
   cudaEvent_t e0, e1;
+};
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 struct Graph {
@@ -841,6 +851,7 @@ blcoc_status finish_solve(blcoc_ctx* h, Solver& sv, void* X, bool hostX, size_t 
 // (bl_cocr_rq or bl_cocg_rq) runs its SpMM, Grams and block updates in complex64.
 blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, bool hostX, int p, int inner_method,
                          double tol, int maxit) {
+  NvtxRange range("blcoc mixed-precision refinement");
   blcoc_status st = ensure_ws32(h, p);
   if (st != BLCOC_OK) return st;
   const size_t bytes = (size_t)h->n * p * sizeof(double2);
@@ -1139,6 +1150,7 @@ blcoc_status iterate_persistent(int nsys, const blcoc_handle* hs, std::vector<So
 extern "C" {
 
 blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_method method, double tol, int maxit) {
+  NvtxRange range("blcoc_solve");
   if (!h) return invalid(h, "NULL handle");
   h->err.clear();
   if (p < 1 || p > BLCOC_MAX_P) return invalid(h, "p must be in [1, 32]");
@@ -1209,7 +1221,10 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   c0.maxit = maxit;
   c0.tol = tol;
   CK(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->s));
-  sv.setup_residual();
+  {
+    NvtxRange r("blcoc setup");
+    sv.setup_residual();
+  }
   CK(h, cudaGetLastError());
   CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));
   CK(h, cudaStreamSynchronize(h->s));
@@ -1220,11 +1235,13 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   } else if (!h->h_ctrl->done) {
     sv.setup_rest();
     CK(h, cudaGetLastError());
+    NvtxRange r("blcoc iterations");
     st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0) + 80 * sv.qr2,
                         maxit);
     if (st != BLCOC_OK) return st;
   }
   // true residual of the returned iterate
+  NvtxRange rr("blcoc true residual");
   sv.B = dB;
   sv.X = dX;
   sv.true_residual();
@@ -1263,6 +1280,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
 static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* hs, const void* const* B,
                                        void* const* X, const int* p, blcoc_method method, double tol, int maxit,
                                        int autotune, double* ms_per_iter_out) {
+  NvtxRange range(form == 1 ? "blcoc_solve_batched_persistent" : "blcoc_solve_batched");
   if (nsys < 1 || !hs || !B || !X || !p) return invalid(nullptr, "blcoc_solve_batched: NULL argument or nsys < 1");
   if (method != BLCOC_COCG_RQ && method != BLCOC_COCR_RQ) return invalid(nullptr, "batched: rq methods only");
   if (!(tol >= 0.0) || std::isinf(tol) || maxit < 0) return invalid(nullptr, "batched: bad tol or maxit");
