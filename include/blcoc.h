@@ -236,6 +236,15 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  Cholesky factor tau2 follows and tau = tau2 tau1 (error about cond(W)
  *                  eps, like a Householder QR).  One extra read/write pass of W per
  *                  iteration.  Not available in blcoc_solve_batched_persistent.
+ *   "spmm_split" : the SpMM's row bundle.  1 (default): p lanes per row (one per column),
+ *                  each summing the row's nonzeros in order.  2 or 4: that many lane groups
+ *                  split each row's nonzeros (interleaved) and their partial sums are
+ *                  combined in a fixed order (where p * split <= 32; otherwise 1).  0: a
+ *                  timed sweep of 1 / 2 / 4 on the first solve, cached for the process per
+ *                  (n, nonzeros per row, p); blcoc_solve_batched with autotune != 0 also
+ *                  tunes it per system.  Results are bitwise reproducible for a given
+ *                  bundle.  blcoc_get_stat(h, "spmm_split") reports the bundle used.
+ *                  (The persistent batch always uses 1.)
  *   "persistent_timeout_ms": blcoc_solve_batched_persistent (read from hs[0]): limit of
  *                  one wait of the kernel, in [1, 600000] ms (default 10000).
  *   "persistent_stall": blcoc_solve_batched_persistent (read from hs[0]), a test of the
@@ -252,7 +261,8 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
 
 /* blcoc_get_stat - counters of the last solve: "launches" (kernels launched by the
  * solve, including those inside graph replays), "graph_replays", "outer_iters",
- * "persistent_graph" (last persistent batch: 1 graph replays, 0 direct launches, -1 none)
+ * "persistent_graph" (last persistent batch: 1 graph replays, 0 direct launches, -1 none),
+ * "spmm_split" (SpMM row bundle of the last solve)
  * (refinement steps of a mixed solve), and with the
  * "timing" option "kt_ns.<kernel>" (total device nanoseconds) and "kt_n.<kernel>"
  * (launches that did work) for <kernel> in resid, spmm_gram, spmm_plain, cocr_passA,

@@ -132,6 +132,8 @@ struct blcoc_ctx {
   int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
   int u_explicit_mixed = 1;   // the same for the complex64 inner solves
   int qr_passes = 1;          // 2: CholQR2 (one re-orthogonalising pass after every Cholesky QR)
+  int spmm_split = 1;         // SpMM row bundle (1, 2, 4); 0: timed sweep, cached per (n, nnz/row, p)
+  int stat_spmm_split = 0;    // row bundle of the last solve
   int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
   int persistent_stall = 0;   // persistent batch, test hook: no first work item is published
   int stat_persistent_graph = -1;   // last persistent batch: 1 graph replays, 0 direct launches
@@ -356,6 +358,12 @@ struct Solver {
   // kinds must match PassKind in blcoc_rowpass.cuh
   enum { K_RESID = 0, K_SPMM_GRAM, K_SPMM_PLAIN, K_COCR_A, K_COCR_C, K_COCG_1, K_COCG_2, K_AXPY, K_QR2 };
   int qr2 = 0;   // CholQR2: after each Cholesky QR, W <- W T1 and a second factor
+  int spmm_split = 1;   // SpMM row bundle: lane groups splitting each row's nonzeros (1, 2, 4)
+  LaunchFn spmm_fn() const {
+    if (spmm_split == 4 && K->spmm_gram_s4) return K->spmm_gram_s4;
+    if (spmm_split == 2 && K->spmm_gram_s2) return K->spmm_gram_s2;
+    return K->spmm_gram;
+  }
   // CholQR2's second pass and factor (setup: the factor of R_0)
   void second_qr(bool setup) {
     if (!qr2 || plain) return;
@@ -377,14 +385,14 @@ struct Solver {
   void setup_rest() {
     const int E = tri_count(p);
     if (method == BLCOC_COCR_RQ) {
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 1);   // V_0 = A Q_0, gram W^T A W
+      pass(spmm_fn(), K_SPMM_GRAM, E, 1);   // V_0 = A Q_0, gram W^T A W
       reduce(E, h->ctrl);
       small(SK_COCR_H0, E);
       pass(K->cocr_passC, K_COCR_C, E, 1);     // S_0 = Q_0, U_0 = V_0, gram U^T U
       reduce(E, h->ctrl);
     } else {
       pass(K->cocg_pass2, K_COCG_2, 0, 1);     // S_0 = Q_0
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, base().S);   // A S_0, gram S^T A S
+      pass(spmm_fn(), K_SPMM_GRAM, E, 0, base().S);   // A S_0, gram S^T A S
       reduce(E, h->ctrl);
     }
   }
@@ -397,7 +405,7 @@ struct Solver {
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
       second_qr(false);
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (for H+ of the beta' step)
+      pass(spmm_fn(), K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (for H+ of the beta' step)
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
       pass(K->cocr_passC, K_COCR_C, 0, 4);               // Q, X, S (no U recurrence)
@@ -411,7 +419,7 @@ struct Solver {
         Timer t;
         const bool timed = time_only < 0;
         if (timed) timed_begin(t, K_SPMM_GRAM);
-        K->spmm_gram(a, h->s);
+        spmm_fn()(a, h->s);
         if (timed) timed_end(t);
         ++launches;
         last_grid = a.grid;
@@ -423,7 +431,7 @@ struct Solver {
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
       second_qr(false);
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 1);
+      pass(spmm_fn(), K_SPMM_GRAM, E, 1);
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
       pass(K->cocr_passC, K_COCR_C, E, 0);
@@ -435,7 +443,7 @@ struct Solver {
       small(SK_CHOL, 2 * E);
       second_qr(false);
       pass(K->cocg_pass2, K_COCG_2, 0, 0);
-      pass(K->spmm_gram, K_SPMM_GRAM, E, 0, base().S);   // A S_{m+1}, gram S^T A S
+      pass(spmm_fn(), K_SPMM_GRAM, E, 0, base().S);   // A S_{m+1}, gram S^T A S
       reduce(E, h->ctrl);
     }
   }
@@ -664,6 +672,12 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     (key[10] == 0 ? h->u_explicit : h->u_explicit_mixed) = (int)value;
     return BLCOC_OK;
   }
+  if (!strcmp(key, "spmm_split")) {
+    if (value != 0 && value != 1 && value != 2 && value != 4) return invalid(h, "spmm_split must be 0, 1, 2 or 4");
+    h->graph.reset();
+    h->spmm_split = (int)value;
+    return BLCOC_OK;
+  }
   if (!strcmp(key, "qr_passes")) {
     if (value != 1 && value != 2) return invalid(h, "qr_passes must be 1 or 2");
     h->graph.reset();
@@ -689,6 +703,7 @@ blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value) {
   if (!strcmp(key, "graph_replays")) { *value = h->stat_replays; return BLCOC_OK; }
   if (!strcmp(key, "outer_iters")) { *value = h->outer_iters; return BLCOC_OK; }
   if (!strcmp(key, "persistent_graph")) { *value = h->stat_persistent_graph; return BLCOC_OK; }
+  if (!strcmp(key, "spmm_split")) { *value = h->stat_spmm_split; return BLCOC_OK; }
   for (int k = 0; k < kNumKinds; ++k) {
     const std::string nm(kKindNames[k]);
     if (("kt_ns." + nm) == key) { *value = (int64_t)(h->kt_ms[k] * 1e6); return BLCOC_OK; }
@@ -935,6 +950,53 @@ blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, 
 
 // ------------------------------------------------------------------------ batched solves
 namespace {
+
+// SpMM row-bundle autotuner: time the SpMM (it writes the handle's V and partial slots,
+// which every solve overwrites) with 1, 2 and 4 lane groups per row and keep the fastest;
+// cached per (n, nnz per row, p, FP64 or tensor-core kernel set).
+std::mutex g_spmm_mutex;
+std::map<std::string, int> g_spmm_cache;
+
+int tune_spmm_split(blcoc_ctx* h, Solver& sv, bool tc) {
+  const std::string key = std::to_string(h->n) + "/" + std::to_string((h->nnz * 10 + h->n / 2) / h->n) + "/" +
+                          std::to_string(sv.p) + "/" + (tc ? "tc" : "fp64");
+  {
+    std::lock_guard<std::mutex> lock(g_spmm_mutex);
+    auto it = g_spmm_cache.find(key);
+    if (it != g_spmm_cache.end()) return it->second;
+  }
+  PassArgs a = sv.base();
+  a.ne = tri_count(sv.p);
+  a.flag = 16;   // run whatever the control block says; no T apply
+  a.grid = sv.K->grid(h->n, Solver::K_SPMM_GRAM, h->num_sms);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 1;
+  float best_ms = 1e30f;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    const int cand[3] = {1, 2, 4};
+    for (int c : cand) {
+      sv.spmm_split = c;
+      LaunchFn f = sv.spmm_fn();
+      if (c != 1 && f == sv.K->spmm_gram) continue;   // bundle wider than a warp
+      f(a, h->s);                                     // warm-up
+      cudaEventRecord(e0, h->s);
+      for (int r = 0; r < 3; ++r) f(a, h->s);
+      cudaEventRecord(e1, h->s);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  sv.spmm_split = best;
+  std::lock_guard<std::mutex> lock(g_spmm_mutex);
+  g_spmm_cache[key] = best;
+  return best;
+}
 
 // Launch shapes chosen by the batch autotuner, per batch signature (form, method, and
 // every system's n, nnz and p).
@@ -1217,6 +1279,8 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   sv.plain = plain ? 1 : 0;
   sv.uexpl = !plain && h->u_explicit != 0;
   sv.qr2 = h->qr_passes == 2 ? 1 : 0;
+  sv.spmm_split = h->spmm_split == 0 ? tune_spmm_split(h, sv, tc) : h->spmm_split;
+  h->stat_spmm_split = sv.spmm_fn() == sv.K->spmm_gram ? 1 : sv.spmm_split;
   Ctrl c0{};
   c0.maxit = maxit;
   c0.tol = tol;
@@ -1236,7 +1300,9 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
     sv.setup_rest();
     CK(h, cudaGetLastError());
     NvtxRange r("blcoc iterations");
-    st = run_iterations(h, sv, (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0) + 80 * sv.qr2,
+    st = run_iterations(h, sv,
+                        (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0) + 80 * sv.qr2 +
+                            160 * h->stat_spmm_split,
                         maxit);
     if (st != BLCOC_OK) return st;
   }
@@ -1328,6 +1394,11 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     sv.back().use_fp64_blocks();
     sv.back().qr2 = h->qr_passes == 2 ? 1 : 0;
     sv.back().uexpl = method == BLCOC_COCR_RQ && h->u_explicit != 0;
+    if (form == 0) {   // SpMM row bundle: the handle's, or timed per (n, nnz/row, p) when autotuning
+      const bool tc_i = sv.back().oz != nullptr;
+      sv.back().spmm_split = (autotune || h->spmm_split == 0) ? tune_spmm_split(h, sv.back(), tc_i) : h->spmm_split;
+      h->stat_spmm_split = sv.back().spmm_fn() == sv.back().K->spmm_gram ? 1 : sv.back().spmm_split;
+    }
     Ctrl c0{};
     c0.maxit = maxit;
     c0.tol = tol;

@@ -158,6 +158,8 @@ struct KernelSet {
   LaunchFn cocg_pass2;   // Q = W T (stored); S <- Q + S beta'
   LaunchFn axpy;         // X (FP64) += D (working precision), the refinement update
   LaunchFn qr2;          // CholQR2 second pass: W <- W T (stored); gram W^H W
+  LaunchFn spmm_gram_s2; // spmm_gram with 2 / 4 lane groups splitting each row's nonzeros
+  LaunchFn spmm_gram_s4; // (nullptr where the row bundle would be wider than a warp)
   int (*grid)(int64_t n, int kind, int num_sms);
   void (*prepare)();     // set the dynamic shared-memory limits (once per device)
 };

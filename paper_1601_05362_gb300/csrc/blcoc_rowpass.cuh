@@ -301,12 +301,16 @@ __device__ __forceinline__ void cta_write_gram(GramAcc<NS, S>& g, double2* red, 
 // ---------------------------------------------------------------------------------- gather
 // Y[r][k] = sum_j a_{row,j} X[j][k] (lanes = columns, PP/32 rows per instruction), written
 // to a swizzled tile.  RESID: Y = B - A X, also accumulating |B|^2 and |Y|^2 per lane.
-template <int PP, typename C, bool RESID>
+// Row bundle: LPR = p lanes (one per column) per row, 32 / LPR rows per instruction.  SPL > 1
+// (not with RESID): SPL lane groups split each row's nonzeros (interleaved), and the SPL
+// partial sums are combined by an xor butterfly in a fixed order.
+template <int PP, typename C, bool RESID, int SPL = 1>
 __device__ __forceinline__ void gather_rows(C* Yt, const CsrDev& A, const C* __restrict__ va, const C* __restrict__ Xg,
                                             const C* __restrict__ Bg, int64_t r0, int p, int lane, double& sb,
                                             double& sr) {
-  constexpr int LPR = Geo<PP>::LPR, RPI = Geo<PP>::RPI;
-  const int sub = lane / LPR, k = lane - sub * LPR;
+  constexpr int LPR = Geo<PP>::LPR, LW = LPR * SPL, RPI = 32 / LW;
+  static_assert(LW <= 32 && (SPL == 1 || !RESID), "row bundle wider than a warp");
+  const int sub = lane / LW, rem = lane - sub * LW, part = rem / LPR, k = rem - part * LPR;
   for (int rr = 0; rr < CHUNK; rr += RPI) {
     const int r = rr + sub;
     const int64_t row = r0 + r;
@@ -318,7 +322,7 @@ __device__ __forceinline__ void gather_rows(C* Yt, const CsrDev& A, const C* __r
         sb = fma((double)acc.y, (double)acc.y, sb);
       }
       const int beg = A.rp[row], end = A.rp[row + 1];
-      for (int j = beg; j < end; ++j) {
+      for (int j = beg + part; j < end; j += SPL) {
         const int c = __ldg(A.ci + j);
         const C av = __ldg(va + j);
         const C x = BLCOC_LD(Xg + (int64_t)c * p + k);
@@ -330,7 +334,16 @@ __device__ __forceinline__ void gather_rows(C* Yt, const CsrDev& A, const C* __r
         sr = fma((double)acc.y, (double)acc.y, sr);
       }
     }
-    Yt[tix(k, r)] = acc;
+    if constexpr (SPL > 1) {
+#pragma unroll
+      for (int o = LPR; o < LW; o <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (part == 0) Yt[tix(k, r)] = acc;
+    } else {
+      Yt[tix(k, r)] = acc;
+    }
   }
 }
 
@@ -417,7 +430,7 @@ __global__ void __launch_bounds__(NWARP * 32) k_resid(const PassArgs a) {
 // out = Y T (flag=1, cocr: V = A Q = (A W) tau^{-1}) or out = Y (flag=0, cocg: a.W = S,
 // out = A S).  flag&F_UEXPL: gram Y^T Y instead (explicit U = A S and U^T U).
 // Partials: [W^T Y or Y^T Y tri].
-template <int PP, typename S, bool OZ = false>
+template <int PP, typename S, bool OZ = false, int SPL = 1>
 __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
@@ -441,7 +454,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   double dummy0 = 0.0, dummy1 = 0.0;
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
-    gather_rows<PP, C, false>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
+    gather_rows<PP, C, false, SPL>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
     load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
     if constexpr (OZ) {
@@ -466,9 +479,9 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   if constexpr (OZ) oz_gram_write<PP, false>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
   else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
-template <int PP, typename S, bool OZ = false>
+template <int PP, typename S, bool OZ = false, int SPL = 1>
 __global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
-  d_spmm_gram<PP, S, OZ>(a, blockIdx.x, gridDim.x);
+  d_spmm_gram<PP, S, OZ, SPL>(a, blockIdx.x, gridDim.x);
 }
 
 // Y = A W, nothing else (blcoc_spmm).
@@ -860,6 +873,19 @@ void launch_pass(const PassArgs& a, cudaStream_t s) {
   else K<<<a.grid, NWARP * 32, pass_smem<PP, S, OZ>(KIND), s>>>(a);
 }
 
+// The SpMM with SPL lane groups per row, where the bundle fits a warp.
+template <int PP, typename S, bool OZ, int SPL>
+constexpr LaunchFn spmm_split_fn() {
+  if constexpr (Geo<PP>::LPR * SPL <= 32) return &launch_pass<PP, S, K_SPMM_GRAM, k_spmm_gram<PP, S, OZ, SPL>, OZ>;
+  else return nullptr;
+}
+template <int PP, typename S, bool OZ, int SPL>
+void set_spmm_split_smem() {
+  if constexpr (Geo<PP>::LPR * SPL <= 32)
+    cudaFuncSetAttribute(k_spmm_gram<PP, S, OZ, SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)pass_smem<PP, S, OZ>(K_SPMM_GRAM));
+}
+
 template <int PP, typename S>
 void prepare_pass_kernels() {
   static bool done[64] = {false};
@@ -880,6 +906,8 @@ void prepare_pass_kernels() {
   cudaFuncSetAttribute(k_cocg_pass2<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, S>(K_COCG_2));
   cudaFuncSetAttribute(k_qr2<PP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass_smem<PP, S>(K_QR2));
+  set_spmm_split_smem<PP, S, false, 2>();
+  set_spmm_split_smem<PP, S, false, 4>();
   done[dev] = true;
 }
 
@@ -895,6 +923,8 @@ const KernelSet& kernel_set() {
       &launch_pass<PP, S, K_COCG_2, k_cocg_pass2<PP, S>>,
       &launch_pass<PP, S, K_AXPY, k_axpy<PP, S>>,
       &launch_pass<PP, S, K_QR2, k_qr2<PP, S>>,
+      spmm_split_fn<PP, S, false, 2>(),
+      spmm_split_fn<PP, S, false, 4>(),
       &pass_grid<PP, S, false>,
       &prepare_pass_kernels<PP, S>,
   };
@@ -914,6 +944,8 @@ void prepare_pass_kernels_tc() {
                        (int)pass_smem<PP, double, true>(K_COCR_A));
   cudaFuncSetAttribute(k_cocr_passC<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_C));
+  set_spmm_split_smem<PP, double, true, 2>();
+  set_spmm_split_smem<PP, double, true, 4>();
   done[dev] = true;
 }
 
@@ -929,6 +961,8 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
       &launch_pass<PP, double, K_QR2, k_qr2<PP, double>>,
+      spmm_split_fn<PP, double, true, 2>(),
+      spmm_split_fn<PP, double, true, 4>(),
       &pass_grid<PP, double, true>,
       &prepare_pass_kernels_tc<PP>,
   };

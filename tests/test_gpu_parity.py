@@ -364,3 +364,49 @@ def test_cholqr2_on_nearly_dependent_right_hand_sides(method):
         h.close()
     assert errs[2] < 1e-8, errs
     assert errs[1] > 100 * errs[2], errs
+
+
+@pytest.mark.parametrize("p,split", [(1, 2), (1, 4), (2, 4), (4, 2), (4, 4), (8, 2), (8, 4), (16, 2)])
+def test_spmm_row_bundle_splits_match_oracle(p, split):
+    """SpMM row bundles with 2 or 4 lane groups splitting each row's nonzeros (option
+    spmm_split): the iterates match the oracle like the default bundle."""
+    torch = need_gpu()
+    n = 1500 + 3 * p
+    A = P.random_complex_symmetric(n, 9, seed=700 + p, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(n, p, 800 + p)
+    m = 12
+    ref = O.bl_cocr_rq(A.to_scipy(), Bh, tol=0.0, maxit=m)
+    h = _handle(A)
+    h.set_option("spmm_split", split)
+    B = to_dev(torch, Bh)
+    X = torch.zeros_like(B)
+    assert h.solve(B, X, tol=0.0, maxit=m) == 5, h.last_error()
+    assert h.stat("spmm_split") == split
+    info = h.info()
+    assert np.max(np.abs(info["hist"] - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
+    assert rel(X.cpu().numpy(), ref.X) < X_TOL
+    h.close()
+
+
+def test_spmm_row_bundle_autotune_is_cached_and_reproducible():
+    """spmm_split = 0: a timed sweep picks the bundle once per (n, nnz/row, p); the solve
+    then equals a solve with that bundle forced, bit for bit."""
+    torch = need_gpu()
+    A = P.random_complex_symmetric(3000, 9, seed=77, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(3000, 4, 78)
+    h = _handle(A)
+    B = to_dev(torch, Bh)
+    h.set_option("spmm_split", 0)
+    X1 = torch.zeros_like(B)
+    assert h.solve(B, X1, tol=1e-10, maxit=500) == 0
+    chosen = h.stat("spmm_split")
+    assert chosen in (1, 2, 4)
+    X2 = torch.zeros_like(B)
+    assert h.solve(B, X2, tol=1e-10, maxit=500) == 0
+    assert h.stat("spmm_split") == chosen
+    h.set_option("spmm_split", chosen)
+    X3 = torch.zeros_like(B)
+    assert h.solve(B, X3, tol=1e-10, maxit=500) == 0
+    assert np.array_equal(X1.cpu().numpy(), X3.cpu().numpy())
+    assert np.array_equal(X2.cpu().numpy(), X3.cpu().numpy())
+    h.close()
