@@ -1040,14 +1040,13 @@ blcoc_status iterate_persistent(int nsys, const blcoc_handle* hs, std::vector<So
     nlive += live[i] ? 1 : 0;
   }
   if (nlive == 0) return BLCOC_OK;
-  const size_t smem = persistent_smem(pmax);
+  const size_t smem = persistent_smem(pmax, method);
   int occ = 0;
   CK(h0, persistent_ctas_per_sm(smem, &occ));
   if (occ < 1) return invalid(h0, "batched (persistent): the kernel does not fit on an SM");
   const int maxk = occ < 3 ? occ : 3;
-  std::vector<int> cand;   // resident CTAs per SM
-  for (int k = (maxk < 2 ? maxk : 2); k >= 1; --k) cand.push_back(k);
-  if (maxk == 3) cand.push_back(3);
+  std::vector<int> cand;   // resident CTAs per SM: as many as fit first
+  for (int k = maxk; k >= 1; --k) cand.push_back(k);
   int pick = 0, trying = -1;
   if (autotune) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -27,6 +27,8 @@
 //   twice the items that can be in flight).  Every wait has a time limit; a wait that
 //   runs out sets the scheduler's error flag, every CTA then returns, and the host
 //   reports BLCOC_ERR_TIMEOUT.
+#include <type_traits>
+
 #define BLCOC_COHERENT_LOADS 1
 #define BLCOC_SMALL_LD 16
 #include "blcoc_rowpass.cuh"
@@ -237,18 +239,29 @@ __global__ void __launch_bounds__(NWARP * 32, 2)
 
 int persistent_stage_count(int method) { return stage_count(method); }
 
-size_t persistent_smem(int pmax) {
+size_t persistent_smem(int pmax, int method) {
   int PP = 1;
   while (PP < pmax) PP *= 2;
   size_t m = sizeof(SmallShared);
   auto up = [&](size_t v) { m = v > m ? v : m; };
-  // pass C / cocg pass 1 take the most shared memory of the row passes
+  auto kinds = [&](auto pp) {
+    constexpr int W = decltype(pp)::value;
+    if (method == 1) {
+      up(pass_smem<W, double>(K_COCR_A));
+      up(pass_smem<W, double>(K_SPMM_GRAM));
+      up(pass_smem<W, double>(K_COCR_C));
+    } else {
+      up(pass_smem<W, double>(K_COCG_1));
+      up(pass_smem<W, double>(K_COCG_2));
+      up(pass_smem<W, double>(K_SPMM_GRAM));
+    }
+  };
   switch (PP) {
-    case 1: up(pass_smem<1, double>(K_COCR_C)); up(pass_smem<1, double>(K_COCG_1)); break;
-    case 2: up(pass_smem<2, double>(K_COCR_C)); up(pass_smem<2, double>(K_COCG_1)); break;
-    case 4: up(pass_smem<4, double>(K_COCR_C)); up(pass_smem<4, double>(K_COCG_1)); break;
-    case 8: up(pass_smem<8, double>(K_COCR_C)); up(pass_smem<8, double>(K_COCG_1)); break;
-    default: up(pass_smem<16, double>(K_COCR_C)); up(pass_smem<16, double>(K_COCG_1)); break;
+    case 1: kinds(std::integral_constant<int, 1>{}); break;
+    case 2: kinds(std::integral_constant<int, 2>{}); break;
+    case 4: kinds(std::integral_constant<int, 4>{}); break;
+    case 8: kinds(std::integral_constant<int, 8>{}); break;
+    default: kinds(std::integral_constant<int, 16>{}); break;
   }
   return m;
 }

@@ -43,8 +43,8 @@ constexpr int PERSISTENT_PMAX = 16;
 
 // Stages of one iteration and items of a stage (host copy of the device rule).
 int persistent_stage_count(int method);
-// Dynamic shared memory for a batch whose widest system has pmax columns.
-size_t persistent_smem(int pmax);
+// Dynamic shared memory for a batch of one method whose widest system has pmax columns.
+size_t persistent_smem(int pmax, int method);
 // Resident CTAs per SM at that shared-memory size (also sets the kernel's smem limit).
 cudaError_t persistent_ctas_per_sm(size_t smem, int* out);
 // Launch the batch: `grid` CTAs take items from the ring until no system runs; every wait

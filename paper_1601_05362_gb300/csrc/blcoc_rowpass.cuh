@@ -108,12 +108,42 @@ struct Fac {
   }
 };
 
+// Upper-triangular factor packed row by row in shared memory (row k holds columns k..PP-1);
+// only entries with j >= k are read.
+template <int PP, typename S>
+struct FacTri {
+  using C = typename Cx<S>::T;
+  const C* m;
+  __device__ __forceinline__ C operator()(int k, int j) const { return m[k * PP - (k * (k - 1)) / 2 + (j - k)]; }
+};
+template <int PP>
+constexpr int tri_packed() { return PP * (PP + 1) / 2; }
+
+// Stage the upper triangle of a p x p FP64 factor, packed (zero outside p).
+template <int PP, typename C>
+__device__ __forceinline__ void load_mat_tri(C* s, const double2* __restrict__ g, int p) {
+  for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
+    const int k = e / PP, j = e - k * PP;
+    if (j >= k) s[k * PP - (k * (k - 1)) / 2 + (j - k)] = (k < p && j < p) ? from_d2<C>(BLCOC_LD(g + k * p + j)) : czero<C>();
+  }
+}
+
+// Pass C's staged factors: T packed, alpha'xi and beta' full (elements of the working
+// precision, rounded up to a 16-byte boundary).
+template <int PP, typename S>
+constexpr int passC_mats_elems() {
+  using C = typename Cx<S>::T;
+  return Geo<PP, S>::MATS_SMEM
+             ? (int)((((size_t)(tri_packed<PP>() + 2 * PP * PP) * sizeof(C) + 15) / 16 * 16) / sizeof(C))
+             : 0;
+}
+
 // ---------------------------------------------------------------------------------- applies
 // t <- t * T with T upper triangular (lane = row).  Columns are produced from the last
 // block to the first, so a column slot is overwritten only after every later column
 // that needs it has been formed.  Cost: exactly sum_j (j+1) complex MACs per row.
-template <int PP, typename S>
-__device__ __forceinline__ void tri_apply_inplace(typename Cx<S>::T* t, const Fac<PP, S>& T, int p, int lane) {
+template <int PP, typename S, typename F>
+__device__ __forceinline__ void tri_apply_inplace(typename Cx<S>::T* t, const F& T, int p, int lane) {
   using C = typename Cx<S>::T;
   constexpr int JB = Geo<PP, S>::JB;
   for (int j0 = ((p - 1) / JB) * JB; j0 >= 0; j0 -= JB) {
@@ -566,20 +596,21 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   using G = Geo<PP, S>;
   const bool first = a.flag & 1;
   const bool uexpl = a.flag & F_UEXPL;
+  // staged factors: T packed (upper triangle), alpha'xi, beta'
   C* mT = smem;
-  C* mAX = smem + PP * PP;
-  C* mB = smem + 2 * PP * PP;
-  C* tiles = smem + mats_off<PP, S>(3);
-  C* b0 = tiles + warp * 3 * G::TILE;
+  C* mAX = smem + tri_packed<PP>();
+  C* mB = mAX + PP * PP;
+  C* tiles = smem + passC_mats_elems<PP, S>();
+  // two tiles per warp: Q is stored as soon as it is formed and read back (from L2, by the
+  // same threads) for the S update, so X, S and Q never need three tiles at once
+  C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
-  C* b2 = b1 + G::TILE;
   if constexpr (G::MATS_SMEM) {
-    load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
+    load_mat_tri<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
     load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
     __syncthreads();
   }
-  Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
   Fac<PP, S> AX{G::MATS_SMEM ? mAX : reinterpret_cast<const C*>(a.mats + M_ALPHAXI * PMAX * PMAX), p};
   Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
   GramAcc<G::NTRI, S> g;
@@ -587,57 +618,59 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
-    if (!first) {
-      load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
-      load_tile<PP>(b2, blk<C>(a.X), r0, n, p, lane);
-    }
     __syncwarp();
     if constexpr (OZ) {
       const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
       oz_apply<PP, false, false>(b0, nullptr, b0, fz, oz_colexp_of(fz), p, lane);
+    } else if constexpr (G::MATS_SMEM) {
+      tri_apply_inplace<PP, S>(b0, FacTri<PP, S>{mT}, p, lane);     // Q_{m+1}
     } else {
-      tri_apply_inplace<PP, S>(b0, T, p, lane);             // Q_{m+1}
+      tri_apply_inplace<PP, S>(b0, Fac<PP, S>{reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p}, p,
+                               lane);
     }
     __syncwarp();
     store_tile<PP>(blk<C>(a.Q), b0, r0, n, p, lane);
     if (!first) {
+      __syncwarp();
+      load_tile<PP>(b0, blk<C>(a.X), r0, n, p, lane);
+      load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
+      __syncwarp();
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_ALPHAXI * OZ_SLOT_U2;
-        oz_apply<PP, false, true>(b2, b2, b1, fz, oz_colexp_of(fz), p, lane);
+        oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
       } else {
-        apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);  // X_{m+1}
+        apply_full<PP, S, false>(b0, b0, b1, AX, p, lane);  // X_{m+1}
       }
       __syncwarp();
-      store_tile<PP>(blk<C>(a.X), b2, r0, n, p, lane);
+      store_tile<PP>(blk<C>(a.X), b0, r0, n, p, lane);
+      __syncwarp();
+      load_tile<PP>(b0, blk<C>(a.Q), r0, n, p, lane);      // Q_{m+1}, just stored
       __syncwarp();
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
-        oz_apply<PP, false, true>(b2, b0, b1, fz, oz_colexp_of(fz), p, lane);
+        oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
       } else {
-        apply_full<PP, S, false>(b2, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
+        apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
       }
       __syncwarp();
-      store_tile<PP>(blk<C>(a.S), b2, r0, n, p, lane);
-    } else {
-      __syncwarp();
-      store_tile<PP>(blk<C>(a.S), b0, r0, n, p, lane);
     }
+    store_tile<PP>(blk<C>(a.S), b0, r0, n, p, lane);       // (setup: S_0 = Q_0)
     __syncwarp();
     if (uexpl) continue;
-    load_tile<PP>(b1, blk<C>(a.V), r0, n, p, lane);
-    if (!first) load_tile<PP>(b2, blk<C>(a.U), r0, n, p, lane);
+    load_tile<PP>(b0, blk<C>(a.V), r0, n, p, lane);
+    if (!first) load_tile<PP>(b1, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
     if (!first) {
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
-        oz_apply<PP, false, true>(b1, b1, b2, fz, oz_colexp_of(fz), p, lane);
+        oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
       } else {
-        apply_full<PP, S, false>(b1, b1, b2, BE, p, lane);  // U_{m+1} = V + U beta'
+        apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);  // U_{m+1} = V + U beta'
       }
       __syncwarp();
     }
-    g.template add<false>(b1, b1, lane);
-    store_tile<PP>(blk<C>(a.U), b1, r0, n, p, lane);
+    g.template add<false>(b0, b0, lane);
+    store_tile<PP>(blk<C>(a.U), b0, r0, n, p, lane);
     __syncwarp();
   }
   if (uexpl) return;
@@ -807,9 +840,10 @@ constexpr size_t pass_smem(int kind) {
   const size_t esz = sizeof(typename Cx<S>::T);
   const size_t tile = (size_t)G::TILE * esz;
   const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2, 0, 1};
-  const int ntiles[K_NKIND] = {1, 2, 1, 2, 3, 3, 2, 0, 1};
+  const int ntiles[K_NKIND] = {1, 2, 1, 2, 2, 3, 2, 0, 1};
   if (kind == K_RESID) return (size_t)NWARP * PP * CHUNK * sizeof(double2);   // FP64 residual tile
-  const size_t mats = (size_t)mats_off<PP, S>(nmats[kind]) * esz;
+  const size_t mats =
+      (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
   size_t s = mats + (size_t)NWARP * ntiles[kind] * tile;
   // the CTA-level Gram reduction reuses the tile area: NWARP * E double2 (two Grams at most
   // are written one after the other, so one E-sized area suffices)
