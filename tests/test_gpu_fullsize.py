@@ -117,14 +117,19 @@ def test_fp64_tc_first_iterations_and_solve(problem):
 
 
 def test_cholqr2_first_iterations_match_oracle(problem):
-    """CholQR2 (qr_passes = 2) at the bench size: history for m <= 20 and X_5 against the
-    oracle."""
+    """CholQR2 (qr_passes = 2) at the bench size: X_5 against the oracle to 1e-10, the
+    history for m <= 20 within max(1e-8, 10x the oracle's own sensitivity) - the second
+    factorisation rounds differently, and under a 1e-16 relative perturbation of B the
+    oracle's own history already moves by up to ~1.5e-8 by m = 20 on this problem."""
     torch = need_gpu()
     from paper_1601_05362_gb300 import blcoc
     pr = problem
     A = pr.A.to_scipy()
     ref = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=20)
     ref5 = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=5)
+    Bp = pr.B * (1.0 + 1e-16 * np.random.default_rng(0).standard_normal(pr.B.shape))
+    hp = np.array(O.bl_cocr_rq(A, Bp, tol=0.0, maxit=20).hist)
+    hsens = np.max(np.abs(hp - np.array(ref.hist)) / np.array(ref.hist))
     with blcoc.Handle.from_csr(pr.A) as h:
         h.set_option("qr_passes", 2)
         B = to_dev(torch, pr.B)
@@ -134,4 +139,6 @@ def test_cholqr2_first_iterations_match_oracle(problem):
         X.zero_()
         assert h.solve(B, X, tol=0.0, maxit=20) == blcoc.BLCOC_NOT_CONVERGED
         hist = np.asarray(h.info()["hist"])
-    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8
+    herr = np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)
+    assert np.max(herr[:11]) < 1e-8, herr        # m <= 10: before the amplification sets in
+    assert np.max(herr) < max(1e-8, 10 * hsens), (np.max(herr), hsens)
