@@ -89,20 +89,47 @@ def problem(method):
     return P.helmholtz3d_n262144_p16(method, maxit=MAXIT)
 
 
-def algorithmic(pr):
-    """Per-iteration algorithmic FP64 flops and HBM bytes of bl_cocr_rq (complex MAC =
-    8 flops; A read once, 14 block passes of n*p*16 bytes: pass A reads Q, U and writes W;
-    the SpMM reads W and writes V; pass C reads W, S, X, V, U and writes Q, X, S, U)."""
+def kernel_width(p):
+    return next(w for w in (1, 2, 4, 8, 16, 32) if p <= w)
+
+
+def fp64_ops(pr):
+    """Per-iteration FP64 operations of bl_cocr_rq per row-pass kernel, as (FMAs, adds),
+    counted from the arithmetic the kernels evaluate.  Kernel widths from 8 up take three
+    real products per complex MAC (Gauss) in the p x p applies and in the self-Grams U^T U
+    and W^H W, plus one add per row, k and 8-column sweep (re + im of the input) and two per
+    output column (the shared term into both parts; the Gram's companion tile likewise);
+    the SpMM's gather and its W^T Y Gram take four products.  Narrower kernels take four
+    products everywhere."""
     n, p, nnz = pr.n, pr.p, pr.A.nnz
+    tri = p * (p + 1) // 2
+    sweeps = range(0, p, 8)
+    if kernel_width(p) >= 8:
+        full = (3 * p * p, len(sweeps) * p + 2 * p)
+        tri_apply = (3 * tri, sum(j0 + min(8, p - j0) for j0 in sweeps) + 2 * p)
+        self_gram = (3 * tri, 2 * p)
+    else:
+        full, tri_apply, self_gram = (4 * p * p, 0), (4 * tri, 0), (4 * tri, 0)
+    gram4 = (4 * tri, 0)
+
+    def rows(*parts):
+        return [n * sum(x[0] for x in parts), n * sum(x[1] for x in parts)]
+
+    ops = {"cocr_passA": rows(full, self_gram), "spmm_gram": rows(tri_apply, gram4),
+           "cocr_passC": rows(tri_apply, full, full, full, self_gram)}
+    ops["spmm_gram"][0] += 4 * nnz * p
+    return {k: tuple(v) for k, v in ops.items()}
+
+
+def algorithmic(pr):
+    """Per-iteration FP64 flops (FMA = 2, add = 1; from fp64_ops) and HBM bytes of
+    bl_cocr_rq (A read once, 14 block passes of n*p*16 bytes: pass A reads Q, U and writes
+    W; the SpMM reads W and writes V; pass C reads W, S, X, V, U and writes Q, X, S, U)."""
+    n, p = pr.n, pr.p
     a_bytes = pr.A.nbytes(16)
     nps = n * p * 16
-    macs = {
-        "cocr_passA": n * (p * p + p * (p + 1) // 2),
-        "spmm_gram": nnz * p + n * p * (p + 1),
-        "cocr_passC": n * (p * (p + 1) + 3 * p * p),
-    }
     bytes_ = {"cocr_passA": 3 * nps, "spmm_gram": a_bytes + 2 * nps, "cocr_passC": 9 * nps}
-    flops = {k: 8.0 * v for k, v in macs.items()}
+    flops = {k: 2.0 * f + a for k, (f, a) in fp64_ops(pr).items()}
     return flops, bytes_, a_bytes + 14 * nps, sum(flops.values())
 
 
@@ -534,11 +561,15 @@ def run_ours(args):
     if dom:
         ach = kern[dom]["tflops"]
         traffic = ncu_traffic(dom)
+        slots = sum(fp64_ops(pr)[dom])
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": f"k_{dom}<16>",
                 "flops_per_launch": flops[dom], "alg_bytes_per_launch": bytes_[dom],
                 "avg_launch_ms": kern[dom]["avg_ms"],
-                "peak_note": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived; probe measured 1.20 TFLOP/s)"}
+                "fp64_pipe_frac": slots / (kern[dom]["avg_ms"] / 1e3) / (FP64_PEAK_TFLOPS * 1e12 / 2),
+                "peak_note": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived; probe measured 1.20 TFLOP/s); "
+                             "flops count an FMA as 2 and an add as 1, fp64_pipe_frac counts both as one "
+                             "of the pipe's 2 operations per clock per SM"}
     t_iter = ms_per_step / mean_iters / 1e3
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

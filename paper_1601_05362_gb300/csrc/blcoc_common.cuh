@@ -52,8 +52,24 @@ enum MatSlot {
   M_BETA,        // beta'_m
   M_H,           // cocr: H_m = Q_m^T V_m;  cocg: G_QQ = Q_m^T Q_m
   M_G1,          // CholQR2 with cocg: W^T W (R^T R at setup) kept for the second factor
-  M_NSLOTS
+  // Three-product forms of the factors the FP64 row passes apply (T, alpha', alpha'xi,
+  // beta'): entry (k, j) of M = Mr + i Mi is kept as Mr and (Mr + Mi, Mi - Mr), so that a
+  // complex product y M costs three real products (Gauss): with s = y.re + y.im,
+  //   re(y M) = s Mr - y.im (Mr + Mi),   im(y M) = s Mr + y.re (Mi - Mr).
+  // Each form takes two slots: (Mr + Mi, Mi - Mr) pairs in the first, Mr in the first half
+  // of the second; row stride p like the complex slots.
+  M3_TINV = 8,
+  M3_ALPHA = 10,
+  M3_ALPHAXI = 12,
+  M3_BETA = 14,
+  M_NSLOTS = 16
 };
+
+// Slot of the three-product form of a factor slot (-1: none kept).
+__host__ __device__ constexpr int m3_slot(int slot) {
+  return slot == M_TINV ? M3_TINV : slot == M_ALPHA ? M3_ALPHA : slot == M_ALPHAXI ? M3_ALPHAXI
+                                                                   : slot == M_BETA ? M3_BETA : -1;
+}
 
 // Gram layouts in the partial buffers: "tri" = upper triangle a <= b, row-major
 // (p(p+1)/2 entries); "full" = p*p row-major.

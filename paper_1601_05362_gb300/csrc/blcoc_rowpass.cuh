@@ -194,10 +194,121 @@ __device__ __forceinline__ void apply_full(typename Cx<S>::T* out, const typenam
   }
 }
 
+// ------------------------------------------------------------------ three-product applies
+// FP64 block widths from 8 up apply the p x p factors in three real products per complex
+// MAC instead of four (Gauss's multiplication): for y = a + ib and M = c + id,
+//   re(y M) = (a + b) c - b (c + d),   im(y M) = (a + b) c + a (d - c),
+// with c, c + d and d - c formed once per factor (three-product slots, written by the p x p
+// stages) and a + b once per row and k.  Per output the shared term (a + b) c is summed
+// once and added to both parts at the end: 3 p^2 + 3 p FP64 operations per full apply and
+// row instead of 4 p^2.  The error bound stays of the order of the four-product one,
+// relative to |y| |M| (the terms are bounded by (|a| + |b|)(|c| + |d|) <= 2 |y| |M|).
+template <int PP, typename S, bool OZ = false>
+constexpr bool m3_apply() { return sizeof(S) == 8 && !OZ && PP >= 8; }
+template <int PP, typename S>
+constexpr bool m3_gram() { return sizeof(S) == 8 && PP >= 8; }
+
+// Three-product form of a factor, read from its slots (row stride p) through the L1 path;
+// every lane of a warp reads the same entry.
+struct Fac3 {
+  const double2* sd;   // (Mr + Mi, Mi - Mr)
+  const double* r;     // Mr
+  int ld;
+  __device__ __forceinline__ Fac3(const double2* mats, int slot, int p)
+      : sd(mats + m3_slot(slot) * PMAX * PMAX),
+        r(reinterpret_cast<const double*>(mats + (m3_slot(slot) + 1) * PMAX * PMAX)),
+        ld(p) {}
+  __device__ __forceinline__ double re(int k, int j) const { return BLCOC_LD(r + k * ld + j); }
+  __device__ __forceinline__ double2 sdif(int k, int j) const { return BLCOC_LD(sd + k * ld + j); }
+};
+
+// acc += y M(k, j) in three products; kk accumulates the shared term (a + b) c.
+template <bool SUB>
+__device__ __forceinline__ void mac3(double2& acc, double& kk, double2 y, double ys, double mr, double2 m) {
+  if constexpr (SUB) {
+    kk = fma(-ys, mr, kk);
+    acc.x = fma(y.y, m.x, acc.x);
+    acc.y = fma(-y.x, m.y, acc.y);
+  } else {
+    kk = fma(ys, mr, kk);
+    acc.x = fma(-y.y, m.x, acc.x);
+    acc.y = fma(y.x, m.y, acc.y);
+  }
+}
+
+// out <- base + in * M (SUB: base - in * M), three products per MAC; aliasing as apply_full.
+template <int PP, bool SUB>
+__device__ __forceinline__ void apply_full3(double2* out, const double2* base, const double2* in, const Fac3& M,
+                                            int p, int lane) {
+  constexpr int JB = Geo<PP>::JB;
+  for (int j0 = 0; j0 < p; j0 += JB) {
+    double2 acc[JB];
+    double kk[JB];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) {
+      acc[jj] = (j0 + jj < p) ? base[tix(j0 + jj, lane)] : cz();
+      kk[jj] = 0.0;
+    }
+    for (int k = 0; k < p; ++k) {
+      const double2 y = in[tix(k, lane)];
+      const double ys = y.x + y.y;
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) mac3<SUB>(acc[jj], kk[jj], y, ys, M.re(k, j0 + jj), M.sdif(k, j0 + jj));
+    }
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj)
+      if (j0 + jj < p) out[tix(j0 + jj, lane)] = make_double2(acc[jj].x + kk[jj], acc[jj].y + kk[jj]);
+  }
+}
+
+// t <- t * T, T upper triangular, three products per MAC; column order as tri_apply_inplace.
+template <int PP>
+__device__ __forceinline__ void tri_apply3_inplace(double2* t, const Fac3& T, int p, int lane) {
+  constexpr int JB = Geo<PP>::JB;
+  for (int j0 = ((p - 1) / JB) * JB; j0 >= 0; j0 -= JB) {
+    double2 acc[JB];
+    double kk[JB];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) {
+      acc[jj] = cz();
+      kk[jj] = 0.0;
+    }
+    for (int k = 0; k < j0; ++k) {
+      const double2 y = t[tix(k, lane)];
+      const double ys = y.x + y.y;
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) mac3<false>(acc[jj], kk[jj], y, ys, T.re(k, j0 + jj), T.sdif(k, j0 + jj));
+    }
+#pragma unroll
+    for (int kq = 0; kq < JB; ++kq) {
+      if (j0 + kq < p) {
+        const double2 y = t[tix(j0 + kq, lane)];
+        const double ys = y.x + y.y;
+#pragma unroll
+        for (int jj = kq; jj < JB; ++jj)
+          mac3<false>(acc[jj], kk[jj], y, ys, T.re(j0 + kq, j0 + jj), T.sdif(j0 + kq, j0 + jj));
+      }
+    }
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj)
+      if (j0 + jj < p) t[tix(j0 + jj, lane)] = make_double2(acc[jj].x + kk[jj], acc[jj].y + kk[jj]);
+  }
+}
+
+// sd <- (re + im, im - re) of every element of the tile t (lane = row), for the
+// three-product Grams of t with itself.
+template <int PP>
+__device__ __forceinline__ void sd_tile(double2* sd, const double2* t, int p, int lane) {
+  for (int k = 0; k < p; ++k) {
+    const double2 v = t[tix(k, lane)];
+    sd[tix(k, lane)] = make_double2(v.x + v.y, v.y - v.x);
+  }
+}
+
 // ---------------------------------------------------------------------------------- grams
 enum GramKind { G_FULL = 0, G_SYM = 1, G_HERM = 2 };
 
-template <int NS, typename S>
+template <int NS, typename S, bool M3 = false>
 struct GramAcc {
   // Entries e = lane + 32 i (i < F) take all 32 rows of a chunk.  The Er = E mod 32
   // remainder entries, when Er divides 32, are spread over G = 32/Er row groups so that
@@ -205,8 +316,11 @@ struct GramAcc {
   // idle lanes); the G partial sums are combined by shuffles at the end.
   // FP64: products accumulate directly in FP64.  complex64: each chunk's products
   // accumulate in FP32 and the chunk total is added to the FP64 accumulator.
+  // M3 (FP64 self-Grams Y^T Y / Y^H Y): three products per MAC, as the applies, from the
+  // tile and its (re + im, im - re) companion; kk holds the term shared by both parts.
   using C = typename Cx<S>::T;
   double2 acc[NS];
+  double kk[M3 ? NS : 1];
   short a[NS], b[NS];
   int E, F, Er, G;
   __device__ __forceinline__ void init(int kind, int p, int lane) {
@@ -217,6 +331,7 @@ struct GramAcc {
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
       acc[i] = cz();
+      if constexpr (M3) kk[i] = 0.0;
       int e = lane + 32 * i;
       if (i == F && G > 1) e = 32 * F + lane % Er;
       int aa = 0, bb = 0;
@@ -288,8 +403,61 @@ struct GramAcc {
       }
     }
   }
+  // Three-product self-Gram, entry (a, b) over row r, y = Y[a], z = Y[b], (s, d) their
+  // companions:  SYM  y z      = (kk + acc.x, kk + acc.y), kk += z.re s_y, acc += (-y.im s_z, y.re d_z);
+  //              HERM conj(y) z: kk -= z.re d_y, acc += (y.im s_z, y.re d_z).
+  // On the diagonal of the Hermitian Gram kk and acc.y take opposite roundings of the same
+  // products, so its imaginary part is exactly zero.
+  template <bool HERM>
+  __device__ __forceinline__ void mac3g(int i, const double2* Y, const double2* SD, int r) {
+    const double2 y = Y[tix(a[i], r)];
+    const double2 sy = SD[tix(a[i], r)];
+    const double zx = Y[tix(b[i], r)].x;
+    const double2 sz = SD[tix(b[i], r)];
+    if constexpr (HERM) {
+      kk[i] = fma(-zx, sy.y, kk[i]);
+      acc[i].x = fma(y.y, sz.x, acc[i].x);
+    } else {
+      kk[i] = fma(zx, sy.x, kk[i]);
+      acc[i].x = fma(-y.y, sz.x, acc[i].x);
+    }
+    acc[i].y = fma(y.x, sz.y, acc[i].y);
+  }
+  template <bool HERM>
+  __device__ __forceinline__ void add3(const double2* Y, const double2* SD, int lane) {
+    static_assert(M3, "three-product Gram");
+#pragma unroll 2
+    for (int r = 0; r < CHUNK; ++r) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i)
+        if (i < F) mac3g<HERM>(i, Y, SD, r);
+    }
+    if (F < NS && Er > 0) {
+      if (G > 1) {
+        const int rows = CHUNK / G, r0 = (lane / Er) * rows;
+        for (int r = r0; r < r0 + rows; ++r) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i)
+            if (i == F) mac3g<HERM>(i, Y, SD, r);
+        }
+      } else if (lane < Er) {
+        for (int r = 0; r < CHUNK; ++r) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i)
+            if (i == F) mac3g<HERM>(i, Y, SD, r);
+        }
+      }
+    }
+  }
   // combine the row-group partial sums of the remainder slot (fixed butterfly order)
   __device__ __forceinline__ void fold() {
+    if constexpr (M3) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        acc[i].x += kk[i];
+        acc[i].y += kk[i];
+      }
+    }
     if (F < NS && G > 1) {
 #pragma unroll
       for (int i = 0; i < NS; ++i) {
@@ -306,8 +474,8 @@ struct GramAcc {
 
 // Sum the warps' accumulators of one Gram in a fixed order and write the CTA partial.
 // `red` is shared scratch of at least NWARP*E double2; caller syncs before reuse.
-template <int NS, typename S>
-__device__ __forceinline__ void cta_write_gram(GramAcc<NS, S>& g, double2* red, double2* __restrict__ out, int warp,
+template <int NS, typename S, bool M3>
+__device__ __forceinline__ void cta_write_gram(GramAcc<NS, S, M3>& g, double2* red, double2* __restrict__ out, int warp,
                                                int lane) {
   g.fold();
 #pragma unroll
@@ -465,12 +633,13 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
+  constexpr bool M3A = m3_apply<PP, S, OZ>();
   C* T_s = smem;
-  C* tiles = smem + mats_off<PP, S>(1);
+  C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
   C* tY = tiles + warp * 2 * G::TILE;
   C* tW = tY + G::TILE;
   const bool applyT = a.flag & 1;
-  if constexpr (G::MATS_SMEM) {
+  if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(T_s, a.mats + M_TINV * PMAX * PMAX, p);
     __syncthreads();
   }
@@ -497,6 +666,8 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
         oz_apply<PP, false, false>(tY, nullptr, tY, fz, oz_colexp_of(fz), p, lane);
+      } else if constexpr (M3A) {
+        tri_apply3_inplace<PP>(tY, Fac3(a.mats, M_TINV, p), p, lane);
       } else {
         tri_apply_inplace<PP, S>(tY, T, p, lane);
       }
@@ -542,16 +713,18 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
+  constexpr bool M3A = m3_apply<PP, S, OZ>();
+  constexpr bool M3G = M3A;   // W^H W: three products where the applies take them (OZ: tensor cores)
   C* mA = smem;
-  C* tiles = smem + mats_off<PP, S>(1);
+  C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
   C* tW = tiles + warp * 2 * G::TILE;
   C* tU = tW + G::TILE;
-  if constexpr (G::MATS_SMEM) {
+  if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
     __syncthreads();
   }
   Fac<PP, S> AL{G::MATS_SMEM ? mA : reinterpret_cast<const C*>(a.mats + M_ALPHA * PMAX * PMAX), p};
-  GramAcc<G::NTRI, S> g;
+  GramAcc<G::NTRI, S, M3G> g;
   g.init(G_HERM, p, lane);
   double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
   if constexpr (OZ) {
@@ -565,11 +738,15 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
     if constexpr (OZ) {
       const uint2* fz = a.oz + OZ_ALPHA * OZ_SLOT_U2;
       oz_apply<PP, true, true>(tW, tW, tU, fz, oz_colexp_of(fz), p, lane);
+    } else if constexpr (M3A) {
+      apply_full3<PP, true>(tW, tW, tU, Fac3(a.mats, M_ALPHA, p), p, lane);   // W_{m+1} = Q_m - U_m alpha'
+      sd_tile<PP>(tU, tW, p, lane);                                           // U_m is no longer needed
     } else {
       apply_full<PP, S, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
     }
     __syncwarp();
     if constexpr (OZ) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tW, tW, p, lane);
+    else if constexpr (M3G) g.template add3<true>(tW, tU, lane);
     else g.template add<true>(tW, tW, lane);
     store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
     __syncwarp();
@@ -596,16 +773,18 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   using G = Geo<PP, S>;
   const bool first = a.flag & 1;
   const bool uexpl = a.flag & F_UEXPL;
-  // staged factors: T packed (upper triangle), alpha'xi, beta'
+  constexpr bool M3A = m3_apply<PP, S, OZ>();
+  constexpr bool M3G = m3_gram<PP, S>();
+  // staged factors (four-product forms): T packed (upper triangle), alpha'xi, beta'
   C* mT = smem;
   C* mAX = smem + tri_packed<PP>();
   C* mB = mAX + PP * PP;
-  C* tiles = smem + passC_mats_elems<PP, S>();
+  C* tiles = smem + (M3A ? 0 : passC_mats_elems<PP, S>());
   // two tiles per warp: Q is stored as soon as it is formed and read back (from L2, by the
   // same threads) for the S update, so X, S and Q never need three tiles at once
   C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
-  if constexpr (G::MATS_SMEM) {
+  if constexpr (G::MATS_SMEM && !M3A) {
     load_mat_tri<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
     load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
@@ -613,7 +792,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   }
   Fac<PP, S> AX{G::MATS_SMEM ? mAX : reinterpret_cast<const C*>(a.mats + M_ALPHAXI * PMAX * PMAX), p};
   Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
-  GramAcc<G::NTRI, S> g;
+  GramAcc<G::NTRI, S, M3G> g;
   g.init(G_SYM, p, lane);
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
@@ -622,6 +801,8 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
     if constexpr (OZ) {
       const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
       oz_apply<PP, false, false>(b0, nullptr, b0, fz, oz_colexp_of(fz), p, lane);
+    } else if constexpr (M3A) {
+      tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);       // Q_{m+1}
     } else if constexpr (G::MATS_SMEM) {
       tri_apply_inplace<PP, S>(b0, FacTri<PP, S>{mT}, p, lane);     // Q_{m+1}
     } else {
@@ -638,6 +819,8 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_ALPHAXI * OZ_SLOT_U2;
         oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
+      } else if constexpr (M3A) {
+        apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_ALPHAXI, p), p, lane);   // X_{m+1}
       } else {
         apply_full<PP, S, false>(b0, b0, b1, AX, p, lane);  // X_{m+1}
       }
@@ -649,6 +832,8 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
         oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
+      } else if constexpr (M3A) {
+        apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);      // S_{m+1} = Q + S beta'
       } else {
         apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);  // S_{m+1} = Q + S beta'
       }
@@ -664,12 +849,20 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
         oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
+      } else if constexpr (M3A) {
+        apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);      // U_{m+1} = V + U beta'
       } else {
         apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);  // U_{m+1} = V + U beta'
       }
       __syncwarp();
     }
-    g.template add<false>(b0, b0, lane);
+    if constexpr (M3G) {
+      sd_tile<PP>(b1, b0, p, lane);   // U_m is no longer needed
+      __syncwarp();
+      g.template add3<false>(b0, b1, lane);
+    } else {
+      g.template add<false>(b0, b0, lane);
+    }
     store_tile<PP>(blk<C>(a.U), b0, r0, n, p, lane);
     __syncwarp();
   }
@@ -691,20 +884,22 @@ __device__ __forceinline__ void d_cocg_pass1(const PassArgs& a, const int vblk, 
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
+  constexpr bool M3A = m3_apply<PP, S>();
+  constexpr bool M3G = m3_gram<PP, S>() && PP <= 16;   // two Grams of 17 slots at PP = 32: no room
   C* mAX = smem;
   C* mA = smem + PP * PP;
-  C* tiles = smem + mats_off<PP, S>(2);
+  C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(2));
   C* b0 = tiles + warp * 3 * G::TILE;
   C* b1 = b0 + G::TILE;
   C* b2 = b1 + G::TILE;
-  if constexpr (G::MATS_SMEM) {
+  if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
     __syncthreads();
   }
   Fac<PP, S> AX{G::MATS_SMEM ? mAX : reinterpret_cast<const C*>(a.mats + M_ALPHAXI * PMAX * PMAX), p};
   Fac<PP, S> AL{G::MATS_SMEM ? mA : reinterpret_cast<const C*>(a.mats + M_ALPHA * PMAX * PMAX), p};
-  GramAcc<G::NTRI, S> gh, gs;
+  GramAcc<G::NTRI, S, M3G> gh, gs;
   gh.init(G_HERM, p, lane);
   gs.init(G_SYM, p, lane);
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
@@ -712,14 +907,23 @@ __device__ __forceinline__ void d_cocg_pass1(const PassArgs& a, const int vblk, 
     load_tile<PP>(b0, blk<C>(a.Q), r0, n, p, lane);
     load_tile<PP>(b1, blk<C>(a.V), r0, n, p, lane);
     __syncwarp();
-    apply_full<PP, S, true>(b0, b0, b1, AL, p, lane);     // W_{m+1} = Q_m - A S_m alpha'
+    if constexpr (M3A) apply_full3<PP, true>(b0, b0, b1, Fac3(a.mats, M_ALPHA, p), p, lane);
+    else apply_full<PP, S, true>(b0, b0, b1, AL, p, lane);     // W_{m+1} = Q_m - A S_m alpha'
     __syncwarp();
     load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
     load_tile<PP>(b2, blk<C>(a.X), r0, n, p, lane);
     __syncwarp();
-    apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);    // X_{m+1}
-    gh.template add<true>(b0, b0, lane);
-    gs.template add<false>(b0, b0, lane);
+    if constexpr (M3A) apply_full3<PP, false>(b2, b2, b1, Fac3(a.mats, M_ALPHAXI, p), p, lane);
+    else apply_full<PP, S, false>(b2, b2, b1, AX, p, lane);    // X_{m+1}
+    if constexpr (M3G) {
+      sd_tile<PP>(b1, b0, p, lane);   // S_m is no longer needed (each lane rewrites its own row)
+      __syncwarp();
+      gh.template add3<true>(b0, b1, lane);
+      gs.template add3<false>(b0, b1, lane);
+    } else {
+      gh.template add<true>(b0, b0, lane);
+      gs.template add<false>(b0, b0, lane);
+    }
     __syncwarp();
     store_tile<PP>(blk<C>(a.X), b2, r0, n, p, lane);
     store_tile<PP>(blk<C>(a.W), b0, r0, n, p, lane);
@@ -743,12 +947,13 @@ __device__ __forceinline__ void d_cocg_pass2(const PassArgs& a, const int vblk, 
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   const bool first = a.flag & 1;
+  constexpr bool M3A = m3_apply<PP, S>();
   C* mT = smem;
   C* mB = smem + PP * PP;
-  C* tiles = smem + mats_off<PP, S>(2);
+  C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(2));
   C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
-  if constexpr (G::MATS_SMEM) {
+  if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mB, a.mats + M_BETA * PMAX * PMAX, p);
     __syncthreads();
@@ -760,11 +965,15 @@ __device__ __forceinline__ void d_cocg_pass2(const PassArgs& a, const int vblk, 
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
     if (!first) load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
     __syncwarp();
-    tri_apply_inplace<PP, S>(b0, T, p, lane);            // Q_{m+1}
+    if constexpr (M3A) tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);
+    else tri_apply_inplace<PP, S>(b0, T, p, lane);            // Q_{m+1}
     __syncwarp();
     store_tile<PP>(blk<C>(a.Q), b0, r0, n, p, lane);
     __syncwarp();
-    if (!first) apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);
+    if (!first) {
+      if constexpr (M3A) apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);
+      else apply_full<PP, S, false>(b0, b0, b1, BE, p, lane);
+    }
     __syncwarp();
     store_tile<PP>(blk<C>(a.S), b0, r0, n, p, lane);
     __syncwarp();
@@ -783,23 +992,29 @@ __device__ __forceinline__ void d_qr2(const PassArgs& a, const int vblk, const i
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
+  constexpr bool M3A = m3_apply<PP, S>();
+  constexpr bool M3G = m3_gram<PP, S>();
   C* mT = smem;
-  C* tiles = smem + mats_off<PP, S>(1);
-  C* tW = tiles + warp * G::TILE;
-  if constexpr (G::MATS_SMEM) {
+  C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
+  C* tW = tiles + warp * (M3G ? 2 : 1) * G::TILE;
+  C* tSD = tW + G::TILE;   // (re + im, im - re) companion of W for the three-product Gram
+  if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     __syncthreads();
   }
   Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
-  GramAcc<G::NTRI, S> g;
+  GramAcc<G::NTRI, S, M3G> g;
   g.init(G_HERM, p, lane);
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
-    tri_apply_inplace<PP, S>(tW, T, p, lane);
+    if constexpr (M3A) tri_apply3_inplace<PP>(tW, Fac3(a.mats, M_TINV, p), p, lane);
+    else tri_apply_inplace<PP, S>(tW, T, p, lane);
+    if constexpr (M3G) sd_tile<PP>(tSD, tW, p, lane);
     __syncwarp();
-    g.template add<true>(tW, tW, lane);
+    if constexpr (M3G) g.template add3<true>(tW, tSD, lane);
+    else g.template add<true>(tW, tW, lane);
     store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
     __syncwarp();
   }
@@ -842,9 +1057,14 @@ constexpr size_t pass_smem(int kind) {
   const int nmats[K_NKIND] = {0, 1, 0, 1, 3, 2, 2, 0, 1};
   const int ntiles[K_NKIND] = {1, 2, 1, 2, 2, 3, 2, 0, 1};
   if (kind == K_RESID) return (size_t)NWARP * PP * CHUNK * sizeof(double2);   // FP64 residual tile
+  // three-product applies read their factors from global memory (L1); the CholQR2 pass
+  // then keeps a second tile for the companion of its three-product Gram
+  const bool oz_kind = OZ && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C);
+  const bool m3 = m3_apply<PP, S>() && !oz_kind;
+  const int nt = (kind == K_QR2 && m3_gram<PP, S>()) ? 2 : ntiles[kind];
   const size_t mats =
-      (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
-  size_t s = mats + (size_t)NWARP * ntiles[kind] * tile;
+      m3 ? 0 : (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
+  size_t s = mats + (size_t)NWARP * nt * tile;
   // the CTA-level Gram reduction reuses the tile area: NWARP * E double2 (two Grams at most
   // are written one after the other, so one E-sized area suffices)
   const size_t red = (size_t)NWARP * tri_count(PP) * sizeof(double2);

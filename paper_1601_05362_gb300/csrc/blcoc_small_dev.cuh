@@ -305,6 +305,21 @@ __device__ void emit_oz(uint2* oz, int slot, const double2* M, int p, int* sh) {
 
 __device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s * PMAX * PMAX; }
 
+// A factor the row passes apply, from shared memory to its slot together with its
+// three-product form (the pairs (Mr + Mi, Mi - Mr) and Mr).
+__device__ void gstore_fac(double2* mats, int sl, const double2* s, int p) {
+  double2* g = slot(mats, sl);
+  double2* sd = slot(mats, m3_slot(sl));
+  double* r = reinterpret_cast<double*>(slot(mats, m3_slot(sl) + 1));
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const double2 v = s[(e / p) * LD + e % p];
+    g[e] = v;
+    sd[e] = make_double2(v.x + v.y, v.y - v.x);
+    r[e] = v.x;
+  }
+  __syncthreads();
+}
+
 // Setup after the residual pass: ||B||_F, Q_0 xi_0 = R_0 (Cholesky QR), T_0 = xi_0^{-1};
 // cocg: G_QQ = Q_0^T Q_0 = T^T (R^T R) T.
 // inner = 1 (refinement step): the stopping test is relative to ||R_0||_F, the norm of
@@ -336,6 +351,8 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
       slot(mats, M_XI)[e] = v;
       slot(mats, M_TAU)[e] = v;
       slot(mats, M_TINV)[e] = v;
+      slot(mats, M3_TINV)[e] = make_double2(v.x, -v.x);
+      reinterpret_cast<double*>(slot(mats, M3_TINV + 1))[e] = v.x;
     }
     if (threadIdx.x == 0) ctrl->pad[1] = S.gs[2 * (2 * E) + 1];   // ||R_0||_F^2
     if (method == 0) {
@@ -351,7 +368,7 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
   }
   tri_inv_upper(S.m[1], S.m[2], p, S.red);
   gstore(slot(mats, M_XI), S.m[1], p);
-  gstore(slot(mats, M_TINV), S.m[2], p);
+  gstore_fac(mats, M_TINV, S.m[2], p);
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     expand_tri(S.gs + 2 * E, S.m[3], p, false);
@@ -411,9 +428,9 @@ __device__ __noinline__ void d_small_alpha(SmallShared& S, int p, const double* 
     if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 2; }
     return;
   }
-  gstore(slot(mats, M_ALPHA), S.m[2], p);
+  gstore_fac(mats, M_ALPHA, S.m[2], p);
   matmul<0, 1>(S.m[3], S.m[2], false, S.m[0], false, p);   // alpha' xi, xi upper triangular
-  gstore(slot(mats, M_ALPHAXI), S.m[3], p);
+  gstore_fac(mats, M_ALPHAXI, S.m[3], p);
   emit_oz(oz, OZ_ALPHA, S.m[2], p, S.colexp);
   emit_oz(oz, OZ_ALPHAXI, S.m[3], p, S.colexp);
   if (threadIdx.x == 0) ctrl->iter = m + 1;
@@ -445,7 +462,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
         if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 4; }
         return;
       }
-      gstore(slot(mats, M_BETA), S.m[4], p);
+      gstore_fac(mats, M_BETA, S.m[4], p);
     }
     __syncthreads();
     return;
@@ -464,7 +481,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   matmul<1, 1>(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
   gstore(slot(mats, M_XI), S.m[4], p);
   gstore(slot(mats, M_TAU), S.m[1], p);
-  gstore(slot(mats, M_TINV), S.m[2], p);
+  gstore_fac(mats, M_TINV, S.m[2], p);
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     const int E = tri_count(p);
@@ -482,7 +499,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
       if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 4; }
       return;
     }
-    gstore(slot(mats, M_BETA), S.m[4], p);
+    gstore_fac(mats, M_BETA, S.m[4], p);
   }
 }
 
@@ -531,10 +548,10 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
         if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 4; }
         return;
       }
-      gstore(slot(mats, M_BETA), S.m[5], p);
+      gstore_fac(mats, M_BETA, S.m[5], p);
     }
   }
-  gstore(slot(mats, M_TINV), S.m[2], p);
+  gstore_fac(mats, M_TINV, S.m[2], p);
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
 }
 
@@ -558,7 +575,7 @@ __device__ __noinline__ void d_small_cocr_beta(SmallShared& S, int p, const doub
     }
     return;
   }
-  gstore(slot(mats, M_BETA), S.m[5], p);
+  gstore_fac(mats, M_BETA, S.m[5], p);
   emit_oz(oz, OZ_BETA, S.m[5], p, S.colexp);
 }
 

@@ -80,17 +80,30 @@ def test_batch_recipe():
 
 
 def test_bench_algorithmic_counts():
+    import types
     import bench
     pr = P.helmholtz3d_n262144_p16()
+    n, p, nnz = pr.n, pr.p, pr.A.nnz
+    ops = bench.fp64_ops(pr)
+    # pass C at p = 16: Q = W T (136 complex MACs), X, S, U updates (256 each), U^T U (136):
+    # 1040 MACs of three FMAs; adds: 24 input sums + 32 output combines (T), 3 x (32 + 32)
+    # (full applies), 32 (the Gram's companion tile)
+    assert ops["cocr_passC"] == (3 * 1040 * n, 280 * n)
+    # pass A: W = Q - U alpha' (256 MACs), W^H W (136); the SpMM: gather (four products),
+    # V = Y T (136, three), W^T Y (136, four)
+    assert ops["cocr_passA"] == (3 * 392 * n, 96 * n)
+    assert ops["spmm_gram"] == (4 * nnz * p + 3 * 136 * n + 4 * 136 * n, 56 * n)
     flops, bytes_, it_bytes, it_flops = bench.algorithmic(pr)
-    n, p = pr.n, pr.p
-    nps = n * p * 16
-    # pass C: Q = W T (tri), X, S, U updates (full), U^T U (tri) -> 1040 complex MACs per row
-    assert flops["cocr_passC"] == 8.0 * n * (p * (p + 1) + 3 * p * p)
-    assert bytes_["cocr_passC"] == 9 * nps
-    assert it_bytes == pr.A.nbytes(16) + 14 * nps
+    assert flops["cocr_passC"] == 2.0 * 3120 * n + 280 * n
+    assert bytes_["cocr_passC"] == 9 * n * p * 16
+    assert it_bytes == pr.A.nbytes(16) + 14 * n * p * 16
     assert abs(it_bytes / 1e6 - 976.78) < 0.01
-    assert abs(it_flops / 1e9 - 3.808) < 0.01
+    assert abs(it_flops / 1e9 - 3.0964) < 0.001
+    # kernel widths below 8 keep four products everywhere
+    small = types.SimpleNamespace(n=1000, p=4, A=types.SimpleNamespace(nnz=5000))
+    o4 = bench.fp64_ops(small)
+    assert o4["cocr_passC"] == (4 * 1000 * (4 * 5 + 3 * 16), 0)
+    assert o4["cocr_passA"] == (4 * 1000 * (16 + 10), 0)
 
 
 def test_source_hash_ignores_comments(tmp_path):
