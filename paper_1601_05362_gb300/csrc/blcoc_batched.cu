@@ -192,7 +192,7 @@ __device__ bool put_item(SchedState* sch, QItem* ring, unsigned cap, long long t
   return true;
 }
 
-__global__ void __launch_bounds__(NWARP * 32, 2)
+__global__ void __launch_bounds__(NWARP * 32, 3)
     k_batched_persistent(const PersSys* __restrict__ sys, int method, SchedState* sch, QItem* ring, unsigned cap,
                          SysRun* run, long long timeout_ns) {
   extern __shared__ __align__(16) unsigned char pers_raw[];
