@@ -12,7 +12,7 @@ import pytest
 
 import oracle.blcoc_oracle as O
 from paper_1601_05362_gb300 import problems as P
-from gpu_common import need_gpu, to_dev, rel
+from gpu_common import need_gpu, to_dev, rel, oracle_iters_range
 
 pytestmark = pytest.mark.gpu
 
@@ -64,8 +64,12 @@ def test_helmholtz2d_n1024_p4_full_solve(method):
     info = h.info()
     assert st == 0, h.last_error()
     # the residual of this indefinite problem is erratic, so where it first crosses tol
-    # moves by a few iterations under different rounding (BLAS, reduction order)
-    assert abs(info["iters"] - ref.iters) <= max(3, ref.iters // 20)
+    # moves by a few iterations under different rounding (BLAS, reduction order): the
+    # count must lie within max(3, 5%) of the oracle's own spread under 1e-16
+    # perturbations of B
+    lo, hi = oracle_iters_range(f, A, pr.B, pr.tol, pr.maxit)
+    slack = max(3, ref.iters // 20)
+    assert lo - slack <= info["iters"] <= hi + slack, (info["iters"], lo, hi)
     hist = info["hist"]
     m = min(21, len(hist), len(ref.hist))
     assert np.max(np.abs(hist[:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m])) < HIST_TOL
@@ -303,7 +307,11 @@ def test_fp64_tc_full_solve_helmholtz2d():
     X = torch.zeros_like(B)
     assert h.solve(B, X, tol=1e-10, maxit=500) == 0
     info = h.info()
-    assert abs(info["iters"] - ref.iters) <= max(3, ref.iters // 20)
+    # the residual stagnates near 1e-10 before crossing it: the oracle's own count spreads
+    # over several iterations under 1e-16 perturbations of B (47 to 54 on two machines)
+    lo, hi = oracle_iters_range(O.bl_cocr_rq, pr.A.to_scipy(), Bh, 1e-10, 500)
+    slack = max(3, ref.iters // 20)
+    assert lo - slack <= info["iters"] <= hi + slack, (info["iters"], lo, hi)
     m = min(21, len(ref.hist))
     assert np.max(np.abs(info["hist"][:m] - np.array(ref.hist[:m])) / np.array(ref.hist[:m])) < HIST_TOL
     assert info["relres_true"] <= 1e-9
