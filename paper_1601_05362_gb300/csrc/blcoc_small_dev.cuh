@@ -25,11 +25,6 @@ constexpr int LD = BLCOC_SMALL_LD;
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ double2 crecip(double2 z) {
-  const double d = z.x * z.x + z.y * z.y;
-  return make_double2(z.x / d, -z.y / d);
-}
-__device__ __forceinline__ double cabs1(double2 z) { return fabs(z.x) + fabs(z.y); }
 __device__ __forceinline__ bool cfinite(double2 z) { return isfinite(z.x) && isfinite(z.y); }
 
 // Second stage, inside the small kernels: gs[c] = sum_s stage1[s][c].
@@ -44,27 +39,18 @@ __device__ void sum_stage1(const double* stage1, int ncomp, double* gs) {
   __syncthreads();
 }
 
-// Reciprocal of a positive finite double by Newton's iteration r <- r (2 - d r) from a
-// single-precision start (two steps: ~48 correct bits -> within 1 ulp).  Used where a
+// 1/d for a positive double: the hardware's reciprocal estimate refined by two Newton
+// steps r <- r (2 - d r), each of which squares the relative error (the estimate's ~2^-22
+// becomes far below an ulp); d outside [1e-300, 1e300] takes a division.  Used where a
 // division would sit on a long sequential chain (pivots of the p x p factorisations).
-// d = m 2^e is split with integer operations so that the float start never leaves the
-// float range; exponents near the ends of the double range fall back to a division.
 __device__ __forceinline__ double recip_pos(double d) {
-  const long long bits = __double_as_longlong(d);
-  const int ex = (int)((bits >> 52) & 0x7FF) - 1023;
-  if (ex < -1000 || ex > 1000) return 1.0 / d;
-  const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);  // [1, 2)
-  double r = (double)__frcp_rn((float)m);
-  double e = fma(-m, r, 1.0);
+  if (!(d > 1e-300 && d < 1e300)) return 1.0 / d;
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
   r = fma(r, e, r);
-  e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
-  return r * __longlong_as_double((long long)(1023 - ex) << 52);   // exact scaling by 2^-ex
-}
-__device__ __forceinline__ double2 crecip_fast(double2 z) {
-  const double d = fma(z.x, z.x, z.y * z.y);
-  const double r = recip_pos(d);
-  return make_double2(z.x * r, -z.y * r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
 }
 
 __device__ __forceinline__ void tri_decode(int e, int p, int& a, int& b) {
@@ -97,25 +83,19 @@ __device__ void gstore(double2* __restrict__ g, const double2* s, int p) {
 }
 
 // C = op(A) op(B), op = transpose (no conjugation) when the flag is set; C must not alias.
-// SA / SB: structure of op(A) / op(B) - 0 full, 1 upper triangular, 2 lower triangular -
-// whose zero half is skipped.  Even and odd k go to two accumulators as in the full
-// product, and the skipped terms are exact zeros, so the result is the full product's.
-template <int SA = 0, int SB = 0>
+// Every entry runs the full k range even where an operand is triangular: the zero half
+// contributes exact zeros, and on GB300 an FP64 warp instruction costs the same with idle
+// lanes, so a uniform loop is the faster one.  Even and odd k go to two accumulators.
 __device__ void matmul(double2* C, const double2* A, bool tA, const double2* B, bool tB, int p) {
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e / p, j = e % p;
-    int k0 = 0, k1 = p;
-    if (SA == 1) k0 = max(k0, i);
-    if (SA == 2) k1 = min(k1, i + 1);
-    if (SB == 1) k1 = min(k1, j + 1);
-    if (SB == 2) k0 = max(k0, j);
     double2 acc0 = cz(), acc1 = cz();
-    int k = k0 & ~1;
-    for (; k + 2 <= k1; k += 2) {
+    int k = 0;
+    for (; k + 2 <= p; k += 2) {
       cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
       cmac(acc1, tA ? A[(k + 1) * LD + i] : A[i * LD + k + 1], tB ? B[j * LD + k + 1] : B[(k + 1) * LD + j]);
     }
-    if (k < k1) cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
+    if (k < p) cmac(acc0, tA ? A[k * LD + i] : A[i * LD + k], tB ? B[j * LD + k] : B[k * LD + j]);
     C[i * LD + j] = make_double2(acc0.x + acc1.x, acc0.y + acc1.y);
   }
   __syncthreads();
@@ -141,28 +121,27 @@ __device__ double fro_norm(const double2* M, int p, double* red) {
 }
 
 // Right-looking Cholesky of a Hermitian G (upper triangle used, destroyed): tau^H tau = G.
+// Per step warp 0 forms the pivot's inverse square root and row j of tau, then all threads
+// update the trailing triangle: two barriers per step.
 __device__ bool chol_upper(double2* G, double2* tau, int p, double* sh) {
   for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) tau[e] = cz();
   __syncthreads();
   for (int j = 0; j < p; ++j) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       const double d = G[j * LD + j].x;
-      if (!(d > 0.0) || !isfinite(d)) {
-        sh[0] = 0.0;
-      } else {
+      const bool ok = d > 0.0 && isfinite(d);
+      if (ok) {
         const double ir = rsqrt(d);
-        tau[j * LD + j] = make_double2(d * ir, 0.0);
-        sh[0] = ir;
+        for (int i = j + 1 + threadIdx.x; i < p; i += 32) {
+          const double2 g = G[j * LD + i];
+          tau[j * LD + i] = make_double2(g.x * ir, g.y * ir);
+        }
+        if (threadIdx.x == 0) tau[j * LD + j] = make_double2(d * ir, 0.0);
       }
+      if (threadIdx.x == 0) sh[0] = ok ? 1.0 : 0.0;
     }
     __syncthreads();
-    const double inv = sh[0];
-    if (inv == 0.0) return false;
-    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) {
-      const double2 g = G[j * LD + i];
-      tau[j * LD + i] = make_double2(g.x * inv, g.y * inv);
-    }
-    __syncthreads();
+    if (sh[0] == 0.0) return false;
     const int m = p - j - 1;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int i = j + 1 + e / m, l = j + 1 + e % m;
@@ -180,84 +159,92 @@ __device__ bool chol_upper(double2* G, double2* tau, int p, double* sh) {
   return true;
 }
 
-// T = tau^{-1} for upper-triangular tau with real positive diagonal.
+// T = tau^{-1} for upper-triangular tau with real positive diagonal, all columns at once by
+// column-oriented back substitution: T starts as I; for k = p-1 .. 1 row k is final, and
+// every entry (i < k, j >= k) subtracts tau_ik T_kj with T_kj = acc_kj / tau_kk formed on the
+// fly (one barrier per k); the rows are scaled by 1 / tau_ii at the end.
 __device__ void tri_inv_upper(const double2* tau, double2* T, int p, double* dinv) {
-  for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) T[e] = cz();
-  for (int i = threadIdx.x; i < p; i += blockDim.x) dinv[i] = 1.0 / tau[i * LD + i].x;
+  for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) {
+    const int i = e / LD, j = e - i * LD;
+    T[e] = make_double2((i == j && i < p) ? 1.0 : 0.0, 0.0);
+  }
+  for (int i = threadIdx.x; i < p; i += blockDim.x) dinv[i] = recip_pos(tau[i * LD + i].x);
   __syncthreads();
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    T[j * LD + j] = make_double2(dinv[j], 0.0);
-    for (int i = j - 1; i >= 0; --i) {
-      double2 s0 = cz(), s1 = cz();
-      int k = i + 1;
-      for (; k + 2 <= j + 1; k += 2) {
-        cmac(s0, tau[i * LD + k], T[k * LD + j]);
-        cmac(s1, tau[i * LD + k + 1], T[(k + 1) * LD + j]);
-      }
-      if (k <= j) cmac(s0, tau[i * LD + k], T[k * LD + j]);
-      const double d = -dinv[i];
-      T[i * LD + j] = make_double2((s0.x + s1.x) * d, (s0.y + s1.y) * d);
+  for (int k = p - 1; k > 0; --k) {
+    const int w = p - k;
+    const double dk = dinv[k];
+    for (int e = threadIdx.x; e < k * w; e += blockDim.x) {
+      const int i = e / w, j = k + (e - i * w);
+      const double2 a = T[k * LD + j];
+      cmsub(T[i * LD + j], tau[i * LD + k], make_double2(a.x * dk, a.y * dk));
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e / p, j = e - i * p;
+    if (j >= i) {
+      const double d = dinv[i];
+      const double2 t = T[i * LD + j];
+      T[i * LD + j] = make_double2(t.x * d, t.y * d);
     }
   }
   __syncthreads();
 }
 
-// Solve M Z = R in place (R <- Z), LU with partial pivoting; M is destroyed.
-// Pivot = largest |re| + |im| in the column (ties to the lowest row).  For non-negative
-// doubles the IEEE bit pattern orders like the value, so the warp argmax compares 64-bit
-// integers (NaN patterns sort above +inf and are then reported as a breakdown).
+// Pivot key of a complex entry for the warp argmax: the high 32 bits of max(|re|, |im|)
+// (for non-negative doubles the bit pattern orders like the value), whose 5 lowest bits
+// are replaced by 31 - row, so that one 32-bit warp max picks the largest magnitude and,
+// among magnitudes equal in their leading 15 mantissa bits, the lowest row.
+__device__ __forceinline__ unsigned piv_key(double2 z, int row) {
+  const unsigned hx = (unsigned)((unsigned long long)__double_as_longlong(z.x) >> 32) & 0x7FFFFFFFu;
+  const unsigned hy = (unsigned)((unsigned long long)__double_as_longlong(z.y) >> 32) & 0x7FFFFFFFu;
+  return ((hx > hy ? hx : hy) & ~31u) | (unsigned)(31 - row);
+}
+
+// 1/z = conj(z) / |z|^2 for a pivot.
+__device__ __forceinline__ double2 crecip_piv(double2 z) {
+  const double r = recip_pos(fma(z.x, z.x, z.y * z.y));
+  return make_double2(z.x * r, -z.y * r);
+}
+
+// Solve M Z = R in place (R <- Z), Gaussian elimination with partial pivoting; M is
+// destroyed.  Pivot: the largest max(|re|, |im|) in the column (piv_key; a pivot that is
+// zero to 15 bits or not finite is a breakdown).  Step k: warp 0 finds the pivot row
+// while each of its lanes forms the reciprocal of its own candidate, then swaps rows k
+// and piv (columns >= k of M, all of R) and scales the new row k by the pivot's reciprocal
+// in one pass, a column per lane; all threads then subtract M_ik x row k from every row
+// below.  Two barriers per step; the eliminated system has a unit upper triangle, so the
+// back substitution is one multiply-subtract per entry and step.  p <= 32.
 __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, int* ish) {
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < p; ++k) {
     if (threadIdx.x < 32) {
-      unsigned long long best = 0ull;
-      int bi = p;
-      for (int i = k + threadIdx.x; i < p; i += 32) {
-        const unsigned long long key = (unsigned long long)__double_as_longlong(cabs1(M[i * LD + k]));
-        if (bi == p || key > best) {
-          best = key;
-          bi = i;
+      const bool cand = lane >= k && lane < p;
+      const double2 z = cand ? M[lane * LD + k] : cz();
+      const unsigned key = cand ? piv_key(z, lane) : 0u;
+      const double2 zr = crecip_piv(cand ? z : make_double2(1.0, 0.0));
+      const unsigned best = __reduce_max_sync(0xffffffffu, key);
+      const int bi = 31 - (int)(best & 31u);
+      const bool ok = (best & ~31u) != 0u && ((best >> 20) & 0x7FFu) != 0x7FFu && bi >= k && bi < p;
+      double2 pinv;
+      pinv.x = __shfl_sync(0xffffffffu, zr.x, bi & 31);
+      pinv.y = __shfl_sync(0xffffffffu, zr.y, bi & 31);
+      __syncwarp();   // every lane has read its candidate before rows k and piv change
+      if (ok) {
+        const int nm = p - k;
+        for (int c = lane; c < nm + nrhs; c += 32) {
+          double2* pk = c < nm ? M + k * LD + k + c : R + k * LD + (c - nm);
+          double2* pb = c < nm ? M + bi * LD + k + c : R + bi * LD + (c - nm);
+          const double2 a = *pb, b = *pk;
+          const double2 sc = cmul(a, pinv);
+          if (bi != k) *pb = b;
+          *pk = c == 0 ? a : sc;   // column k keeps the pivot (not read again)
         }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi < p && (bi == p || ob > best || (ob == best && oi < bi))) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (threadIdx.x == 0) {
-        const double v = __longlong_as_double((long long)best);
-        ish[0] = bi;
-        ish[1] = (bi < p && v > 0.0 && isfinite(v)) ? 1 : 0;
-        if (ish[1]) {   // reciprocal of the pivot, formed once for the whole CTA
-          const double2 r = crecip_fast(M[bi * LD + k]);
-          sh[2 * PMAX] = r.x;
-          sh[2 * PMAX + 1] = r.y;
-        }
-      }
+      if (lane == 0) ish[1] = ok ? 1 : 0;
     }
     __syncthreads();
     if (!ish[1]) return false;
-    const int piv = ish[0];
-    if (piv != k) {
-      for (int c = threadIdx.x; c < p + nrhs; c += blockDim.x) {
-        if (c < p) {
-          const double2 t = M[k * LD + c];
-          M[k * LD + c] = M[piv * LD + c];
-          M[piv * LD + c] = t;
-        } else {
-          const int cc = c - p;
-          const double2 t = R[k * LD + cc];
-          R[k * LD + cc] = R[piv * LD + cc];
-          R[piv * LD + cc] = t;
-        }
-      }
-      __syncthreads();
-    }
-    const double2 pinv = make_double2(sh[2 * PMAX], sh[2 * PMAX + 1]);
-    for (int i = k + 1 + threadIdx.x; i < p; i += blockDim.x) M[i * LD + k] = cmul(M[i * LD + k], pinv);
-    __syncthreads();
     const int m = p - k - 1, w = m + nrhs;
     for (int e = threadIdx.x; e < m * w; e += blockDim.x) {
       const int i = k + 1 + e / w, c = e % w;
@@ -267,15 +254,10 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
     }
     __syncthreads();
   }
-  // back substitution with the diagonal reciprocals formed once, in parallel
-  double2* dinv = reinterpret_cast<double2*>(sh);
-  for (int k = threadIdx.x; k < p; k += blockDim.x) dinv[k] = crecip(M[k * LD + k]);
-  __syncthreads();
-  for (int k = p - 1; k >= 0; --k) {
-    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) R[k * LD + c] = cmul(R[k * LD + c], dinv[k]);
-    __syncthreads();
+  // back substitution with the unit upper triangle: row k of R is final at step k
+  for (int k = p - 1; k > 0; --k) {
     for (int e = threadIdx.x; e < k * nrhs; e += blockDim.x) {
-      const int i = e / nrhs, c = e % nrhs;
+      const int i = e / nrhs, c = e - i * nrhs;
       cmsub(R[i * LD + c], M[i * LD + k], R[k * LD + c]);
     }
     __syncthreads();
@@ -376,8 +358,8 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
       gstore(slot(mats, M_G1), S.m[3], p);
       return;
     }
-    matmul<2, 0>(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
-    matmul<0, 1>(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
+    matmul(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
+    matmul(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
     gstore(slot(mats, M_H), S.m[5], p);
   }
 }
@@ -388,8 +370,8 @@ __device__ __noinline__ void d_small_cocr_H0(SmallShared& S, int p, const double
   sum_stage1(stage1, ncomp, S.gs);
   expand_tri(S.gs, S.m[0], p, false);
   gload(S.m[1], slot(mats, M_TINV), p);
-  matmul<2, 0>(S.m[2], S.m[1], true, S.m[0], false, p);
-  matmul<0, 1>(S.m[3], S.m[2], false, S.m[1], false, p);
+  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
+  matmul(S.m[3], S.m[2], false, S.m[1], false, p);
   gstore(slot(mats, M_H), S.m[3], p);
 }
 
@@ -429,7 +411,7 @@ __device__ __noinline__ void d_small_alpha(SmallShared& S, int p, const double* 
     return;
   }
   gstore_fac(mats, M_ALPHA, S.m[2], p);
-  matmul<0, 1>(S.m[3], S.m[2], false, S.m[0], false, p);   // alpha' xi, xi upper triangular
+  matmul(S.m[3], S.m[2], false, S.m[0], false, p);   // alpha' xi, xi upper triangular
   gstore_fac(mats, M_ALPHAXI, S.m[3], p);
   emit_oz(oz, OZ_ALPHA, S.m[2], p, S.colexp);
   emit_oz(oz, OZ_ALPHAXI, S.m[3], p, S.colexp);
@@ -478,7 +460,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   }
   tri_inv_upper(S.m[1], S.m[2], p, S.red);
   gload(S.m[3], slot(mats, M_XI), p);
-  matmul<1, 1>(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
+  matmul(S.m[4], S.m[1], false, S.m[3], false, p);   // xi_{m+1} = tau xi_m
   gstore(slot(mats, M_XI), S.m[4], p);
   gstore(slot(mats, M_TAU), S.m[1], p);
   gstore_fac(mats, M_TINV, S.m[2], p);
@@ -490,9 +472,9 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
       gstore(slot(mats, M_G1), S.m[0], p);
       return;
     }
-    matmul<2, 0>(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
-    matmul<0, 1>(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
-    matmul<2, 0>(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
+    matmul(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
+    matmul(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
+    matmul(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
     gload(S.m[3], slot(mats, M_H), p);                // G_QQ (old)
     gstore(slot(mats, M_H), S.m[0], p);
     if (!lu_solve(S.m[3], S.m[4], p, p, S.red, S.ish)) {
@@ -523,25 +505,25 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
   }
   tri_inv_upper(S.m[1], S.m[2], p, S.red);            // T2
   gload(S.m[3], slot(mats, setup ? M_XI : M_TAU), p);  // tau1
-  matmul<1, 1>(S.m[4], S.m[1], false, S.m[3], false, p);   // tau = tau2 tau1
+  matmul(S.m[4], S.m[1], false, S.m[3], false, p);   // tau = tau2 tau1
   if (setup) {
     gstore(slot(mats, M_XI), S.m[4], p);
   } else {
     gstore(slot(mats, M_TAU), S.m[4], p);
     gload(S.m[5], slot(mats, M_XI), p);
-    matmul<1, 1>(S.m[3], S.m[1], false, S.m[5], false, p);   // xi <- tau2 xi
+    matmul(S.m[3], S.m[1], false, S.m[5], false, p);   // xi <- tau2 xi
     gstore(slot(mats, M_XI), S.m[3], p);
   }
   if (method == 0) {
     gload(S.m[5], slot(mats, M_TINV), p);                   // T1
-    matmul<1, 1>(S.m[3], S.m[5], false, S.m[2], false, p);   // T1 T2
+    matmul(S.m[3], S.m[5], false, S.m[2], false, p);   // T1 T2
     gload(S.m[0], slot(mats, M_G1), p);                     // W^T W (R^T R at setup)
-    matmul<2, 0>(S.m[5], S.m[3], true, S.m[0], false, p);
-    matmul<0, 1>(S.m[0], S.m[5], false, S.m[3], false, p);  // (T1 T2)^T G (T1 T2)
+    matmul(S.m[5], S.m[3], true, S.m[0], false, p);
+    matmul(S.m[0], S.m[5], false, S.m[3], false, p);  // (T1 T2)^T G (T1 T2)
     if (setup) {
       gstore(slot(mats, M_H), S.m[0], p);                   // G_QQ
     } else {
-      matmul<2, 0>(S.m[5], S.m[4], true, S.m[0], false, p); // tau^T G_QQ+
+      matmul(S.m[5], S.m[4], true, S.m[0], false, p); // tau^T G_QQ+
       gload(S.m[3], slot(mats, M_H), p);                    // G_QQ (old)
       gstore(slot(mats, M_H), S.m[0], p);
       if (!lu_solve(S.m[3], S.m[5], p, p, S.red, S.ish)) {
@@ -561,10 +543,10 @@ __device__ __noinline__ void d_small_cocr_beta(SmallShared& S, int p, const doub
   sum_stage1(stage1, ncomp, S.gs);
   expand_tri(S.gs, S.m[0], p, false);
   gload(S.m[1], slot(mats, M_TINV), p);
-  matmul<2, 0>(S.m[2], S.m[1], true, S.m[0], false, p);
-  matmul<0, 1>(S.m[3], S.m[2], false, S.m[1], false, p);   // H+
+  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
+  matmul(S.m[3], S.m[2], false, S.m[1], false, p);   // H+
   gload(S.m[4], slot(mats, M_TAU), p);
-  matmul<2, 0>(S.m[5], S.m[4], true, S.m[3], false, p);    // tau^T H+
+  matmul(S.m[5], S.m[4], true, S.m[3], false, p);    // tau^T H+
   gload(S.m[0], slot(mats, M_H), p);
   gstore(slot(mats, M_H), S.m[3], p);
   if (!lu_solve(S.m[0], S.m[5], p, p, S.red, S.ish)) {
