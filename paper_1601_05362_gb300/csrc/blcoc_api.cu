@@ -1078,7 +1078,7 @@ blcoc_status iterate_persistent(int nsys, const blcoc_handle* hs, std::vector<So
     for (int v : hsys[i].vg) mx = v > mx ? v : mx;
     M += mx;
   }
-  const unsigned cap = (unsigned)(2 * M + nsys + 64);
+  const unsigned cap = (unsigned)(2 * M + 2 * nsys + 64);
   // pinned image of [scheduler state][per-system counters][ring]
   const size_t off_run = sizeof(SchedState), off_ring = off_run + (size_t)nsys * sizeof(SysRun);
   const size_t bytes = off_ring + (size_t)cap * sizeof(QItem);
@@ -1108,11 +1108,14 @@ blcoc_status iterate_persistent(int nsys, const blcoc_handle* hs, std::vector<So
     *hs0 = SchedState{};
     for (unsigned k = 0; k < cap; ++k) hring[k] = QItem{~0ull, (unsigned long long)k, 0, 0, 0, 0};
     unsigned long long tail = 0;
+    const int items0 = method == BLCOC_COCR_RQ ? 2 : 1;   // cocr: the alpha' step and the elimination of H_m
     for (int i = 0; i < nsys; ++i) {
-      hrun[i] = SysRun{0, live[i] ? 1 : 0};
+      hrun[i] = SysRun{0, live[i] ? items0 : 0};
       if (live[i] && !h0->persistent_stall) {   // the test hook publishes nothing: every wait runs out
-        hring[tail] = QItem{tail, tail, i, 0, 0, 0};
-        ++tail;
+        for (int it = 0; it < items0; ++it) {
+          hring[tail] = QItem{tail, tail, i, 0, it, 0};
+          ++tail;
+        }
       }
     }
     hs0->tail = tail;

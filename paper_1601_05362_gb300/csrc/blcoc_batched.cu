@@ -82,17 +82,9 @@ __device__ void reduce_item(const PersSys& y, int which, int tri_mult, int sl) {
   const double* part = reinterpret_cast<const double*>(y.a.partials);
   const int q0 = (int)((int64_t)sl * nparts / RED_SPLIT), q1 = (int)((int64_t)(sl + 1) * nparts / RED_SPLIT);
   for (int c = threadIdx.x; c < ncomp; c += blockDim.x) {
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int q = q0;
-    for (; q + 4 <= q1; q += 4) {
-      const double v0 = __ldcg(part + (int64_t)q * ncomp + c), v1 = __ldcg(part + (int64_t)(q + 1) * ncomp + c);
-      const double v2 = __ldcg(part + (int64_t)(q + 2) * ncomp + c), v3 = __ldcg(part + (int64_t)(q + 3) * ncomp + c);
-      a0 += v0;
-      a1 += v1;
-      a2 += v2;
-      a3 += v3;
-    }
-    for (; q < q1; ++q) a0 += __ldcg(part + (int64_t)q * ncomp + c);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};   // a[g]: q = q0 + g, q0 + g + 4, ... in turn
+    for (int q = q0; q < q1; ++q) a[(q - q0) & 3] += __ldcg(part + (int64_t)q * ncomp + c);
+    const double a0 = a[0], a1 = a[1], a2 = a[2], a3 = a[3];
     y.stage1[(int64_t)sl * ncomp + c] = (a0 + a1) + (a2 + a3);
   }
 }
@@ -107,7 +99,7 @@ __device__ __forceinline__ bool stage_is_small(int method, int st) {
   return method == 1 ? (st == 0 || st == 3 || st == 6) : (st == 0 || st == 3);
 }
 __device__ __forceinline__ int stage_items(const PersSys& y, int method, int st) {
-  if (stage_is_small(method, st)) return 1;
+  if (stage_is_small(method, st)) return (method == 1 && st == 0) ? 2 : 1;   // cocr alpha': + the elimination of H_m
   if (method == 1) return st == 1 ? y.vg[0] : st == 4 ? y.vg[1] : st == 7 ? y.vg[2] : RED_SPLIT;
   return st == 1 ? y.vg[0] : st == 4 ? y.vg[2] : st == 5 ? y.vg[1] : RED_SPLIT;
 }
@@ -117,13 +109,16 @@ __device__ void run_item(SmallShared& S, const PersSys& y, int method, int st, i
   double2* mats = const_cast<double2*>(y.a.mats);
   if (method == 1) {
     switch (st) {
-      case 0: d_small_alpha(S, p, y.stage1, 2 * E, mats, y.a.ctrl, y.hist, 0, nullptr); break;
+      case 0:   // item 0: the alpha' step; item 1: the elimination of H_m for the beta' step
+        if (item == 0) d_small_alpha(S, p, y.stage1, 2 * E, mats, y.a.ctrl, y.hist, 0, nullptr);
+        else d_small_hfactor(S, p, mats, y.a.ctrl);
+        break;
       case 1: row_item(y, 0, K_COCR_A, 1, 0, false, item); break;        // W = Q - U alpha', W^H W
       case 2: reduce_item(y, 0, 1, item); break;
       case 3: d_small_chol(S, p, 1, y.stage1, 2 * E, mats, y.a.ctrl, 0, nullptr); break;
       case 4: row_item(y, 1, K_SPMM_GRAM, 1, 1, false, item); break;     // V = A W T, W^T A W
       case 5: reduce_item(y, 1, 1, item); break;
-      case 6: d_small_cocr_beta(S, p, y.stage1, 2 * E, mats, y.a.ctrl, nullptr); break;
+      case 6: d_small_cocr_beta(S, p, y.stage1, 2 * E, mats, y.a.ctrl, nullptr, 0, p); break;
       case 7: row_item(y, 2, K_COCR_C, 1, 0, false, item); break;        // Q, X, S, U, U^T U
       default: reduce_item(y, 2, 1, item); break;
     }

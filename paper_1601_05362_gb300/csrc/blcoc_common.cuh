@@ -32,7 +32,7 @@ struct Ctrl {
   int maxit;
   int bd_code;    // breakdown site: 1 setup QR, 2 alpha solve, 3 QR, 4 beta solve, 5 non-finite xi
   int nhist;      // entries of the residual history written so far
-  int pad_i;
+  int hlu_ok;     // cocr: the LU factors of H_m in slots M_HLU (beside the alpha' step) are valid
   double tol;
   double nb;      // ||B||_F
   double relres;  // ||xi_iter||_F / ||B||_F
@@ -62,7 +62,10 @@ enum MatSlot {
   M3_ALPHA = 10,
   M3_ALPHAXI = 12,
   M3_BETA = 14,
-  M_NSLOTS = 16
+  M_HLU = 16,    // cocr: H_m after elimination with partial pivoting (multipliers below the
+                 // diagonal, the pivot-scaled rows above), formed beside the alpha' step;
+                 // slot 17: the pivots' reciprocals (entries 0..p-1) and rows (entries PMAX..)
+  M_NSLOTS = 18
 };
 
 // Slot of the three-product form of a factor slot (-1: none kept).

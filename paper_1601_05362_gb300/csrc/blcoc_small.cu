@@ -6,27 +6,23 @@
 namespace blcoc {
 
 // ------------------------------------------------------------------------ cross-CTA reduce
-// stage1[s][c] = sum of partials[q][c] over q in slice s (fixed order).
-__global__ void k_reduce_stage1(const double* __restrict__ partials, int nparts, int ncomp,
-                                double* __restrict__ stage1, const Ctrl* ctrl) {
+// stage1[s][c] = sum of partials[q][c] over q in slice s, in a fixed order: warp g of the
+// CTA sums q = q0 + g, q0 + g + 4, ... in turn, and the four warp sums are combined as
+// (a0 + a1) + (a2 + a3).  Each thread thus issues about nparts / 64 independent loads.
+__global__ void __launch_bounds__(128) k_reduce_stage1(const double* __restrict__ partials, int nparts, int ncomp,
+                                                       double* __restrict__ stage1, const Ctrl* ctrl) {
   if (ctrl != nullptr && ctrl->done) return;
-  const int c = blockIdx.x * 32 + threadIdx.x;
-  if (c >= ncomp) return;
+  __shared__ double part[4][32];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
   const int s = blockIdx.y;
   const int q0 = (int)((int64_t)s * nparts / RED_SPLIT), q1 = (int)((int64_t)(s + 1) * nparts / RED_SPLIT);
-  // four interleaved accumulators: the loads are independent and the add chains short
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int q = q0;
-  for (; q + 4 <= q1; q += 4) {
-    const double v0 = partials[(int64_t)q * ncomp + c], v1 = partials[(int64_t)(q + 1) * ncomp + c];
-    const double v2 = partials[(int64_t)(q + 2) * ncomp + c], v3 = partials[(int64_t)(q + 3) * ncomp + c];
-    a0 += v0;
-    a1 += v1;
-    a2 += v2;
-    a3 += v3;
-  }
-  for (; q < q1; ++q) a0 += partials[(int64_t)q * ncomp + c];
-  stage1[(int64_t)s * ncomp + c] = (a0 + a1) + (a2 + a3);
+  double a = 0.0;
+  if (c < ncomp)
+    for (int q = q0 + g; q < q1; q += 4) a += partials[(int64_t)q * ncomp + c];
+  part[g][lane] = a;
+  __syncthreads();
+  if (g == 0 && c < ncomp) stage1[(int64_t)s * ncomp + c] = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
 }
 
 #define SMALL_PROLOGUE                                                  \
@@ -44,10 +40,12 @@ __global__ void k_small_cocr_H0(int p, const double* stage1, int ncomp, double2*
   d_small_cocr_H0(S, p, stage1, ncomp, mats, ctrl);
 }
 
+// CTA 0: the alpha' step; CTA 1 (cocr launches two): the elimination of H_m for the beta' step.
 __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, double* hist,
                               int plain, uint2* oz) {
   SMALL_PROLOGUE
-  d_small_alpha(S, p, stage1, ncomp, mats, ctrl, hist, plain, oz);
+  if (blockIdx.x == 1) d_small_hfactor(S, p, mats, ctrl);
+  else d_small_alpha(S, p, stage1, ncomp, mats, ctrl, hist, plain, oz);
 }
 
 __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
@@ -62,9 +60,12 @@ __global__ void k_small_chol2(int p, int method, const double* stage1, int ncomp
   d_small_chol2(S, p, method, stage1, ncomp, mats, ctrl, setup, oz);
 }
 
+// One CTA per group of columns of beta' (gridDim.x groups).
 __global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, uint2* oz) {
   SMALL_PROLOGUE
-  d_small_cocr_beta(S, p, stage1, ncomp, mats, ctrl, oz);
+  const int per = (p + gridDim.x - 1) / gridDim.x;
+  const int j0 = blockIdx.x * per, j1 = j0 + per < p ? j0 + per : p;
+  if (j0 < j1) d_small_cocr_beta(S, p, stage1, ncomp, mats, ctrl, oz, j0, j1);
 }
 
 __global__ void k_small_trr(int p, const double* stage1, int ncomp, Ctrl* ctrl) {
@@ -146,7 +147,7 @@ void prepare_small_kernels() { set_small_attrs(); }
 void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s) {
   const int ncomp = 2 * ne;
   dim3 grid((ncomp + 31) / 32, RED_SPLIT);
-  k_reduce_stage1<<<grid, 32, 0, s>>>(reinterpret_cast<const double*>(partials), nparts, ncomp, stage1, ctrl);
+  k_reduce_stage1<<<grid, 128, 0, s>>>(reinterpret_cast<const double*>(partials), nparts, ncomp, stage1, ctrl);
 }
 
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
@@ -165,9 +166,13 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
     case SK_CHOL2: k_small_chol2<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, oz); break;
     case SK_CHOL2_SETUP: k_small_chol2<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, oz); break;
     case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
-    case SK_ALPHA: k_small_alpha<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz); break;
+    case SK_ALPHA:
+      k_small_alpha<<<m == 1 ? 2 : 1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz);
+      break;
     case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2); break;
-    case SK_COCR_BETA: k_small_cocr_beta<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, oz); break;
+    case SK_COCR_BETA:   // a CTA per column; one CTA where the exact-slice form is emitted
+      k_small_cocr_beta<<<oz != nullptr ? 1 : p, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, oz);
+      break;
     case SK_TRR: k_small_trr<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, ctrl); break;
   }
 }

@@ -101,6 +101,28 @@ __device__ void matmul(double2* C, const double2* A, bool tA, const double2* B, 
   __syncthreads();
 }
 
+// Columns [j0, j1) of C = op(A) B (op = transpose without conjugation when tA): each entry
+// is four partial sums over k = g, g + 4, ... (g = 0..3, one lane each, in turn) combined
+// by an xor butterfly as (s0 + s1) + (s2 + s3) - the same value whatever range of columns
+// a CTA takes, so one CTA per column and one CTA for all columns agree bit for bit.
+__device__ void matmul_cols(double2* C, const double2* A, bool tA, const double2* B, int p, int j0, int j1) {
+  const int nc = j1 - j0, items = p * nc * 4;
+  for (int base = threadIdx.x & ~31; base < ((items + 31) & ~31); base += blockDim.x) {
+    const int it = base + (threadIdx.x & 31);
+    const int g = it & 3, ent = it >> 2;
+    const int i = ent / nc, j = j0 + (ent - (ent / nc) * nc);
+    double2 acc = cz();
+    if (it < items)
+      for (int k = g; k < p; k += 4) cmac(acc, tA ? A[k * LD + i] : A[i * LD + k], B[k * LD + j]);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+    if (it < items && g == 0) C[i * LD + j] = acc;
+  }
+  __syncthreads();
+}
+
 // ||M||_F in a fixed order that does not depend on the block size (the one-CTA kernels and
 // the persistent kernel run these stages with different block sizes and must agree bit for
 // bit): lane l of warp 0 sums entries l, l + 32, ... in turn, then a fixed butterfly.
@@ -215,7 +237,10 @@ __device__ __forceinline__ double2 crecip_piv(double2 z) {
 // in one pass, a column per lane; all threads then subtract M_ik x row k from every row
 // below.  Two barriers per step; the eliminated system has a unit upper triangle, so the
 // back substitution is one multiply-subtract per entry and step.  p <= 32.
-__device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, int* ish) {
+// piv / pinv (shared memory, optional): the pivot row and the pivot's reciprocal of each
+// step, for lu_replay.
+__device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, int* ish, int* piv = nullptr,
+                         double2* pinvs = nullptr) {
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < p; ++k) {
     if (threadIdx.x < 32) {
@@ -241,7 +266,13 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
           *pk = c == 0 ? a : sc;   // column k keeps the pivot (not read again)
         }
       }
-      if (lane == 0) ish[1] = ok ? 1 : 0;
+      if (lane == 0) {
+        ish[1] = ok ? 1 : 0;
+        if (piv != nullptr) {
+          piv[k] = bi;
+          pinvs[k] = pinv;
+        }
+      }
     }
     __syncthreads();
     if (!ish[1]) return false;
@@ -268,10 +299,41 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
   return ish[1] != 0;
 }
 
+// Columns [j0, j1) of R <- M^{-1} R from the elimination lu_solve recorded (F: M after
+// lu_solve, piv / pinvs: its pivots): the same swaps, scalings and multiply-subtracts in the
+// same order, so every column is bitwise what lu_solve would have made of it.
+__device__ void lu_replay(const double2* F, const int* piv, const double2* pinvs, double2* R, int p, int j0, int j1) {
+  const int nc = j1 - j0;
+  for (int k = 0; k < p; ++k) {
+    const int b = piv[k];
+    for (int c = j0 + threadIdx.x; c < j1; c += blockDim.x) {
+      const double2 a = R[b * LD + c];
+      if (b != k) R[b * LD + c] = R[k * LD + c];
+      R[k * LD + c] = cmul(a, pinvs[k]);
+    }
+    __syncthreads();
+    const int m = p - k - 1;
+    for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
+      const int i = k + 1 + e / nc, c = j0 + e % nc;
+      cmsub(R[i * LD + c], F[i * LD + k], R[k * LD + c]);
+    }
+    __syncthreads();
+  }
+  for (int k = p - 1; k > 0; --k) {
+    for (int e = threadIdx.x; e < k * nc; e += blockDim.x) {
+      const int i = e / nc, c = j0 + e % nc;
+      cmsub(R[i * LD + c], F[i * LD + k], R[k * LD + c]);
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------------ shared layout
 struct SmallShared {
   double gs[2 * (2 * LD * (LD + 1) / 2 + 2)];
   double red[2 * PMAX + 8];
+  double2 pinvs[LD];
+  int piv[LD];
   int ish[4];
   int colexp[64];
   double2 m[6][LD * LD];
@@ -298,6 +360,24 @@ __device__ void gstore_fac(double2* mats, int sl, const double2* s, int p) {
     g[e] = v;
     sd[e] = make_double2(v.x + v.y, v.y - v.x);
     r[e] = v.x;
+  }
+  __syncthreads();
+}
+
+// Columns [j0, j1) of a p x p matrix from shared memory to its slot (and, for a factor the
+// row passes apply, to its three-product form).
+__device__ void gstore_cols(double2* mats, int sl, const double2* s, int p, int j0, int j1) {
+  double2* g = slot(mats, sl);
+  const int s3 = m3_slot(sl);
+  const int nc = j1 - j0;
+  for (int e = threadIdx.x; e < p * nc; e += blockDim.x) {
+    const int i = e / nc, j = j0 + (e - (e / nc) * nc);
+    const double2 v = s[i * LD + j];
+    g[i * p + j] = v;
+    if (s3 >= 0) {
+      slot(mats, s3)[i * p + j] = make_double2(v.x + v.y, v.y - v.x);
+      reinterpret_cast<double*>(slot(mats, s3 + 1))[i * p + j] = v.x;
+    }
   }
   __syncthreads();
 }
@@ -537,28 +617,67 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
 }
 
-// cocr after V_{m+1} (Algorithm 3, the beta' step): H+ = T^T (W^T A W) T, beta' = H^{-1} tau^T H+.
-__device__ __noinline__ void d_small_cocr_beta(SmallShared& S, int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, uint2* oz) {
+// cocr, beside the alpha' step (Algorithm 3): the elimination of H_m = Q_m^T V_m (slot M_H,
+// final here) for the beta' step that follows the next QR, so that the beta' step replays
+// it instead of factorising on its critical path.  A singular H_m is recorded in the
+// control block and reported by the beta' step as its breakdown, as a failed solve there
+// would be.
+__device__ __noinline__ void d_small_hfactor(SmallShared& S, int p, double2* mats, Ctrl* ctrl) {
   if (BLCOC_LD(&ctrl->done)) return;
-  sum_stage1(stage1, ncomp, S.gs);
-  expand_tri(S.gs, S.m[0], p, false);
-  gload(S.m[1], slot(mats, M_TINV), p);
-  matmul(S.m[2], S.m[1], true, S.m[0], false, p);
-  matmul(S.m[3], S.m[2], false, S.m[1], false, p);   // H+
-  gload(S.m[4], slot(mats, M_TAU), p);
-  matmul(S.m[5], S.m[4], true, S.m[3], false, p);    // tau^T H+
-  gload(S.m[0], slot(mats, M_H), p);
-  gstore(slot(mats, M_H), S.m[3], p);
-  if (!lu_solve(S.m[0], S.m[5], p, p, S.red, S.ish)) {
-    if (threadIdx.x == 0) {
-      ctrl->done = 3;
+  gload(S.m[1], slot(mats, M_H), p);
+  const bool ok = lu_solve(S.m[1], nullptr, p, 0, S.red, S.ish, S.piv, S.pinvs);
+  gstore(slot(mats, M_HLU), S.m[1], p);
+  double2* aux = slot(mats, M_HLU + 1);
+  for (int k = threadIdx.x; k < p; k += blockDim.x) {
+    aux[k] = S.pinvs[k];
+    aux[PMAX + k] = make_double2((double)S.piv[k], 0.0);
+  }
+  if (threadIdx.x == 0) ctrl->hlu_ok = ok ? 1 : 0;
+}
+
+// cocr after V_{m+1} (Algorithm 3, the beta' step), columns [j0, j1):
+// H+ = T^T (W^T A W T) by matrix-vector products (matmul_cols), beta' = H_m^{-1} (tau^T H+)
+// by replaying the elimination of H_m made beside the alpha' step.  A launch may split the
+// columns over CTAs; only a launch whose CTA takes all columns emits the exact-slice form.
+__device__ __noinline__ void d_small_cocr_beta(SmallShared& S, int p, const double* stage1, int ncomp, double2* mats,
+                                               Ctrl* ctrl, uint2* oz, int j0, int j1) {
+  if (BLCOC_LD(&ctrl->done)) return;
+  if (!BLCOC_LD(&ctrl->hlu_ok)) {
+    if (threadIdx.x == 0 && atomicCAS(&ctrl->done, 0, 3) == 0) {
       ctrl->bd_code = 4;
       ctrl->iter -= 1;
     }
     return;
   }
-  gstore_fac(mats, M_BETA, S.m[5], p);
-  emit_oz(oz, OZ_BETA, S.m[5], p, S.colexp);
+  sum_stage1(stage1, ncomp, S.gs);
+  expand_tri(S.gs, S.m[0], p, false);                  // W^T A W
+  gload(S.m[1], slot(mats, M_TINV), p);
+  gload(S.m[4], slot(mats, M_TAU), p);
+  gload(S.m[3], slot(mats, M_HLU), p);
+  {
+    const double2* aux = slot(mats, M_HLU + 1);
+    for (int k = threadIdx.x; k < p; k += blockDim.x) {
+      S.pinvs[k] = BLCOC_LD(aux + k);
+      S.piv[k] = (int)BLCOC_LD(aux + PMAX + k).x;
+    }
+  }
+  matmul_cols(S.m[2], S.m[0], false, S.m[1], p, j0, j1);   // (W^T A W) T
+  matmul_cols(S.m[5], S.m[1], true, S.m[2], p, j0, j1);    // H+
+  matmul_cols(S.m[2], S.m[4], true, S.m[5], p, j0, j1);    // tau^T H+
+  lu_replay(S.m[3], S.piv, S.pinvs, S.m[2], p, j0, j1);    // beta'
+  gstore_cols(mats, M_H, S.m[5], p, j0, j1);
+  gstore_cols(mats, M_BETA, S.m[2], p, j0, j1);
+  bool bad = false;
+  for (int e = threadIdx.x; e < p * (j1 - j0); e += blockDim.x)
+    if (!cfinite(S.m[2][(e / (j1 - j0)) * LD + j0 + e % (j1 - j0)])) bad = true;
+  if (__syncthreads_or(bad)) {
+    if (threadIdx.x == 0 && atomicCAS(&ctrl->done, 0, 3) == 0) {
+      ctrl->bd_code = 4;
+      ctrl->iter -= 1;
+    }
+    return;
+  }
+  if (j0 == 0 && j1 == p) emit_oz(oz, OZ_BETA, S.m[2], p, S.colexp);
 }
 
 // Norm of the residual from a norm-only residual pass (Sec. 3, true residual).
