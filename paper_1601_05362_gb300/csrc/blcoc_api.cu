@@ -1228,6 +1228,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   blcoc_status st = ensure_ws(h, p);
   if (st != BLCOC_OK) return st;
   if (h->hist_cap < maxit + 1) {
+    h->graph.reset();   // a captured graph writes the history through the old pointer
     if (h->hist) cudaFree(h->hist);
     h->hist = nullptr;
     h->hist_cap = 0;
@@ -1376,6 +1377,7 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     blcoc_status st = ensure_ws(h, p[i]);
     if (st != BLCOC_OK) return st;
     if (h->hist_cap < maxit + 1) {
+      h->graph.reset();   // a captured graph writes the history through the old pointer
       if (h->hist) cudaFree(h->hist);
       h->hist = nullptr;
       h->hist_cap = 0;

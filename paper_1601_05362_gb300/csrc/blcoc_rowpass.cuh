@@ -662,6 +662,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     } else {
       g.template add<false>((a.flag & F_UEXPL) ? tY : tW, tY, lane);
     }
+    __syncwarp();   // every lane has read Y for the Gram before the in-place apply
     if (applyT) {
       if constexpr (OZ) {
         const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;

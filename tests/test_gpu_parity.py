@@ -418,3 +418,25 @@ def test_spmm_row_bundle_autotune_is_cached_and_reproducible():
     assert np.array_equal(X1.cpu().numpy(), X3.cpu().numpy())
     assert np.array_equal(X2.cpu().numpy(), X3.cpu().numpy())
     h.close()
+
+
+def test_history_after_a_longer_solve_on_the_same_handle():
+    """A second solve with a larger maxit grows the history buffer; the iterations' CUDA
+    graph captured by the first solve must not keep writing to the old buffer: the second
+    history equals that of a fresh handle, bit for bit."""
+    torch = need_gpu()
+    pr = P.helmholtz2d_n1024_p4("cocr_rq")
+    B = to_dev(torch, pr.B)
+    h = _handle(pr.A)
+    X = torch.zeros_like(B)
+    h.solve(B, X, tol=0.0, maxit=5)
+    X.zero_()
+    h.solve(B, X, tol=0.0, maxit=400)
+    grown = np.asarray(h.info()["hist"])
+    h2 = _handle(pr.A)
+    X2 = torch.zeros_like(B)
+    h2.solve(B, X2, tol=0.0, maxit=400)
+    fresh = np.asarray(h2.info()["hist"])
+    assert len(grown) == len(fresh) == 401
+    assert np.array_equal(grown, fresh)
+    assert torch.equal(X, X2)
