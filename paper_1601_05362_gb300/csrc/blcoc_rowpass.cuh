@@ -681,8 +681,10 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   if constexpr (OZ) oz_gram_write<PP, false>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
   else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
+// Two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to that
+// bound cost no occupancy.
 template <int PP, typename S, bool OZ = false, int SPL = 1>
-__global__ void __launch_bounds__(NWARP * 32) k_spmm_gram(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 3) k_spmm_gram(const PassArgs a) {
   d_spmm_gram<PP, S, OZ, SPL>(a, blockIdx.x, gridDim.x);
 }
 
@@ -756,9 +758,15 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   if constexpr (OZ) oz_gram_write<PP, true>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
   else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
+// FP64: two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to
+// that bound cost no occupancy.  The tensor-core variant keeps the compiler's own choice.
 template <int PP, typename S, bool OZ = false>
-__global__ void __launch_bounds__(NWARP * 32) k_cocr_passA(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 3) k_cocr_passA(const PassArgs a) {
   d_cocr_passA<PP, S, OZ>(a, blockIdx.x, gridDim.x);
+}
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_cocr_passA_tc(const PassArgs a) {
+  d_cocr_passA<PP, double, true>(a, blockIdx.x, gridDim.x);
 }
 
 // bl_cocr_rq pass C (Algorithm 3, the X, S and U updates) with Q_{m+1} = W_{m+1} T_{m+1} (stored
@@ -1083,7 +1091,9 @@ const void* pass_kernel(int kind) {
     case K_RESID: return (const void*)k_resid<PP, S>;
     case K_SPMM_GRAM: return (const void*)k_spmm_gram<PP, S, OZ>;
     case K_SPMM_PLAIN: return (const void*)k_spmm_plain<PP, S>;
-    case K_COCR_A: return (const void*)k_cocr_passA<PP, S, OZ>;
+    case K_COCR_A:
+      if constexpr (OZ) return (const void*)k_cocr_passA_tc<PP>;
+      else return (const void*)k_cocr_passA<PP, S>;
     case K_COCR_C: return (const void*)k_cocr_passC<PP, S, OZ>;
     case K_COCG_1: return (const void*)k_cocg_pass1<PP, S>;
     case K_COCG_2: return (const void*)k_cocg_pass2<PP, S>;
@@ -1195,7 +1205,7 @@ void prepare_pass_kernels_tc() {
   if (dev < 0 || dev >= 64 || done[dev]) return;
   cudaFuncSetAttribute(k_spmm_gram<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_SPMM_GRAM));
-  cudaFuncSetAttribute(k_cocr_passA<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_cocr_passA_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_A));
   cudaFuncSetAttribute(k_cocr_passC<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_C));
@@ -1210,7 +1220,7 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_RESID, k_resid<PP, double>>,
       &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>, true>,
       &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
-      &launch_pass<PP, double, K_COCR_A, k_cocr_passA<PP, double, true>, true>,
+      &launch_pass<PP, double, K_COCR_A, k_cocr_passA_tc<PP>, true>,
       &launch_pass<PP, double, K_COCR_C, k_cocr_passC<PP, double, true>, true>,
       &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
