@@ -883,6 +883,12 @@ template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   d_cocr_passC<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
+// The tensor-core pass C: its shared memory allows 3 CTAs per SM, and so does this bound
+// on its registers (otherwise about 238, 2 per SM).
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32, 3) k_cocr_passC_tc(const PassArgs a) {
+  d_cocr_passC<PP, double, true>(a, blockIdx.x, gridDim.x);
+}
 
 // bl_cocg_rq pass 1 (Algorithm 2, the X update and the new residual block), Q_m stored by
 // the previous pass 2:
@@ -1094,7 +1100,9 @@ const void* pass_kernel(int kind) {
     case K_COCR_A:
       if constexpr (OZ) return (const void*)k_cocr_passA_tc<PP>;
       else return (const void*)k_cocr_passA<PP, S>;
-    case K_COCR_C: return (const void*)k_cocr_passC<PP, S, OZ>;
+    case K_COCR_C:
+      if constexpr (OZ) return (const void*)k_cocr_passC_tc<PP>;
+      else return (const void*)k_cocr_passC<PP, S>;
     case K_COCG_1: return (const void*)k_cocg_pass1<PP, S>;
     case K_COCG_2: return (const void*)k_cocg_pass2<PP, S>;
     case K_QR2: return (const void*)k_qr2<PP, S>;
@@ -1207,7 +1215,7 @@ void prepare_pass_kernels_tc() {
                        (int)pass_smem<PP, double, true>(K_SPMM_GRAM));
   cudaFuncSetAttribute(k_cocr_passA_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_A));
-  cudaFuncSetAttribute(k_cocr_passC<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_cocr_passC_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_C));
   set_spmm_split_smem<PP, double, true, 2>();
   set_spmm_split_smem<PP, double, true, 4>();
@@ -1221,7 +1229,7 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>, true>,
       &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
       &launch_pass<PP, double, K_COCR_A, k_cocr_passA_tc<PP>, true>,
-      &launch_pass<PP, double, K_COCR_C, k_cocr_passC<PP, double, true>, true>,
+      &launch_pass<PP, double, K_COCR_C, k_cocr_passC_tc<PP>, true>,
       &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
