@@ -284,7 +284,7 @@ blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value);
  *   norm_out   : device pointer; receives ||B - A X||_F in norm_out[0].
  *   cuda_stream: stream the two kernels are queued on (NULL = legacy default); the call
  *                returns without waiting for them.
- * Scratch: a static device array of BLCOC_NOALLOC_MAX_CTAS x 2 doubles (16 KB) that every
+ * Scratch: a static device array of BLCOC_NOALLOC_MAX_CTAS doubles (8 KB) that every
  * GPU loading the library holds until exit; the row pass uses at most that many CTAs, so
  * any n fits.  Each call overwrites the slots it reads; calls that overlap on the GPU
  * (other streams, other threads) race on the shared array.  The first call on a device

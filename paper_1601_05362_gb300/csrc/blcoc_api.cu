@@ -74,9 +74,26 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// What decides the kernel sequence of a captured batch of iterations: compared field by
+// field, so a new option cannot make two different sequences look alike.
+struct GraphKey {
+  int method = -1;   // blcoc_method of the iteration (the inner rq method for mixed solves)
+  int mixed = 0;     // complex64 inner iteration of the mixed-precision refinement
+  int uexpl = 0;     // U = A S by a second sparse product
+  int plain = 0;     // plain block method (tau = T = xi = I)
+  int tc = 0;        // tensor-core block updates
+  int qr2 = 0;       // CholQR2
+  int split = 0;     // SpMM row bundle
+  bool operator==(const GraphKey& o) const {
+    return method == o.method && mixed == o.mixed && uexpl == o.uexpl && plain == o.plain && tc == o.tc &&
+           qr2 == o.qr2 && split == o.split;
+  }
+};
+
 struct Graph {
   cudaGraphExec_t exec = nullptr;
-  int p = -1, method = -1, batch = 0, timing = 0;
+  GraphKey key;
+  int p = -1, batch = 0, timing = 0;
   const void* X = nullptr;
   int64_t gen = -1;
   int launches = 0;
@@ -105,7 +122,11 @@ struct blcoc_ctx {
   // workspace
   int p_cap = 0;
   int64_t gen = 0;
-  double2 *W = nullptr, *S = nullptr, *U = nullptr, *V = nullptr, *Q = nullptr, *Bst = nullptr, *Xst = nullptr;
+  double2 *W = nullptr, *S = nullptr, *U = nullptr, *V = nullptr, *Q = nullptr;
+  // staging copies of host-memory B and X; st_cap = the columns they hold (independent of
+  // p_cap, which device-pointer solves also raise)
+  double2 *Bst = nullptr, *Xst = nullptr;
+  int st_cap = 0;
   double2* mats = nullptr;
   double2* partials = nullptr;
   size_t partials_cap = 0;   // double2 entries
@@ -144,7 +165,6 @@ struct blcoc_ctx {
   double kt_ms[kNumKinds] = {0};
   int64_t kt_n[kNumKinds] = {0};
   // results of the last solve
-  int last_p = 0;
   int iters = 0;
   double relres = 0.0, trr = 0.0;
   std::vector<double> hist_h;
@@ -763,13 +783,13 @@ namespace {
 // Replays batches of `poll` iterations (captured once as a CUDA graph, or launched
 // directly) until the control block reports the end of the solve.  `gkey` identifies
 // the kernel sequence of the graph (method and working precision).
-blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
+blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, const GraphKey& gkey, int maxit) {
   const int batch = h->poll;
   const bool use_graph = h->use_graph != 0;
   std::vector<Timer> direct_timers;
   if (use_graph) {
     Graph& g = h->graph;
-    if (!(g.exec && g.p == sv.p && g.method == gkey && g.batch == batch && g.X == sv.X && g.gen == h->gen &&
+    if (!(g.exec && g.p == sv.p && g.key == gkey && g.batch == batch && g.X == sv.X && g.gen == h->gen &&
           g.timing == h->timing)) {
       g.reset();
       h->evnext = 0;
@@ -797,7 +817,7 @@ blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, int gkey, int maxit) {
         return cuda_fail(h, e, "cudaGraphInstantiate");
       }
       g.p = sv.p;
-      g.method = gkey;
+      g.key = gkey;
       g.batch = batch;
       g.X = sv.X;
       g.gen = h->gen;
@@ -877,7 +897,12 @@ blcoc_status solve_mixed(blcoc_ctx* h, const double2* dB, double2* dX, void* X, 
   sv.uexpl = h->u_explicit_mixed != 0;
   sv.qr2 = h->qr_passes == 2 ? 1 : 0;
   double2* D = reinterpret_cast<double2*>(h->w32[5]);
-  const int gkey = 100 + inner_method + (sv.uexpl ? 10 : 0) + 80 * sv.qr2;
+  GraphKey gkey;
+  gkey.method = inner_method;
+  gkey.mixed = 1;
+  gkey.uexpl = sv.uexpl ? 1 : 0;
+  gkey.qr2 = sv.qr2;
+  gkey.split = sv.spmm_split;
   std::vector<double> outer_hist;
   int total_inner = 0, outer = 0, done = 2, last_bd = 0;
   double bnorm = 0.0, relres = 0.0;
@@ -1237,14 +1262,15 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   }
   const size_t bytes = (size_t)h->n * p * sizeof(double2);
   const bool hostB = is_host_ptr(B), hostX = is_host_ptr(X);
-  if ((hostB || hostX) && (!h->Bst || h->last_p < p)) {
+  if ((hostB || hostX) && h->st_cap < p) {
     if (h->Bst) cudaFree(h->Bst);
     if (h->Xst) cudaFree(h->Xst);
     h->Bst = h->Xst = nullptr;
-    CK(h, cudaMalloc(&h->Bst, (size_t)h->n * h->p_cap * sizeof(double2)));
-    CK(h, cudaMalloc(&h->Xst, (size_t)h->n * h->p_cap * sizeof(double2)));
+    h->st_cap = 0;
+    CK(h, cudaMalloc(&h->Bst, (size_t)h->n * p * sizeof(double2)));
+    CK(h, cudaMalloc(&h->Xst, (size_t)h->n * p * sizeof(double2)));
+    h->st_cap = p;
   }
-  h->last_p = p > h->last_p ? p : h->last_p;
   CK(h, cudaEventRecord(h->ev, h->user_stream));
   CK(h, cudaStreamWaitEvent(h->s, h->ev, 0));
   const double2* dB = (const double2*)B;
@@ -1303,10 +1329,14 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
     sv.setup_rest();
     CK(h, cudaGetLastError());
     NvtxRange r("blcoc iterations");
-    st = run_iterations(h, sv,
-                        (int)method + (sv.uexpl ? 10 : 0) + 20 * sv.plain + (tc ? 40 : 0) + 80 * sv.qr2 +
-                            160 * h->stat_spmm_split,
-                        maxit);
+    GraphKey gkey;
+    gkey.method = (int)method;
+    gkey.uexpl = sv.uexpl ? 1 : 0;
+    gkey.plain = sv.plain;
+    gkey.tc = tc ? 1 : 0;
+    gkey.qr2 = sv.qr2;
+    gkey.split = h->stat_spmm_split;
+    st = run_iterations(h, sv, gkey, maxit);
     if (st != BLCOC_OK) return st;
   }
   // true residual of the returned iterate

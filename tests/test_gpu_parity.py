@@ -121,6 +121,31 @@ def test_host_pointers_equal_device_pointers(method):
     assert info_h["iters"] == h.info()["iters"]
 
 
+def test_host_staging_follows_its_own_capacity():
+    """Host-memory B and X go through handle-owned staging buffers.  A device-pointer solve
+    with a wider block in between must not let a later host solve reuse buffers sized for
+    a narrower one: host p = 4, device p = 16, host p = 8 on one handle, the last checked
+    bitwise against the same solve from device pointers."""
+    torch = need_gpu()
+    A = P.helmholtz_2d(40, 5.0, 0.05)
+    h = _handle(A)
+    out = {}
+    for p, where in ((4, "host"), (16, "device"), (8, "host"), (8, "device")):
+        Bh = P.complex_normal(A.n, p, 70 + p)
+        if where == "host":
+            X = np.zeros_like(Bh)
+            st = h.solve(Bh, X, method="cocr_rq", tol=1e-10, maxit=400)
+        else:
+            Xd = torch.zeros((A.n, p), dtype=torch.complex128, device="cuda")
+            st = h.solve(to_dev(torch, Bh), Xd, method="cocr_rq", tol=1e-10, maxit=400)
+            X = Xd.cpu().numpy()
+        assert st == 0, (p, where, h.last_error())
+        assert h.info()["relres_true"] <= 1e-9
+        out[(p, where)] = X
+    assert np.array_equal(out[(8, "host")], out[(8, "device")])
+    h.close()
+
+
 def test_graph_and_direct_launches_agree_bitwise():
     torch = need_gpu()
     pr = P.helmholtz2d_n1024_p4("cocr_rq")

@@ -4,8 +4,10 @@ Callers that cannot allocate device memory (their allocator or memory pool is he
 they run inside another library's allocation-free section) use this entry point: it
 takes raw device CSR arrays instead of a handle and keeps its scratch in a static device
 array.  The test calls it through the C ABI twice in a row and checks it against the
-handle-based blcoc_residual_norm within the tolerance the residual-norm test uses.
-It lives in its own file so that pytest collects it last.
+handle-based blcoc_residual_norm and against ||B - A X||_F formed on the host with
+numpy/scipy, within the tolerance the residual-norm test uses, and checks that the calls
+leave the device's free memory unchanged.  It lives in its own file so that pytest
+collects it last.
 """
 import ctypes as C
 
@@ -31,19 +33,31 @@ def test_noalloc_residual_norm_matches_handle_version(shape):
     X = to_dev(torch, P.complex_normal(A.n, p, 12))
     with blcoc.Handle.from_csr(A) as h:
         ref = h.residual_norm(B, X)
+    Bh, Xh = B.cpu().numpy(), X.cpu().numpy()
+    ref_host = float(np.linalg.norm(Bh - A.to_scipy() @ Xh))
     rp, ci, va = to_dev(torch, A.row_ptr), to_dev(torch, A.col_idx), to_dev(torch, A.vals)
     out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
+    def call():
+        return lib.blcoc_residual_norm_noalloc(A.n, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), B.data_ptr(),
+                                               X.data_ptr(), p, out.data_ptr(), stream)
+
+    # a first call may load the library's kernel module (lazy module loading), which
+    # takes device memory once per process; the calls after it must take none
+    assert call() == blcoc.BLCOC_OK, lib.blcoc_last_error(None)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
     values = []
     for _ in range(2):
         out.fill_(-1.0)
-        st = lib.blcoc_residual_norm_noalloc(A.n, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), B.data_ptr(),
-                                             X.data_ptr(), p, out.data_ptr(), stream)
+        st = call()
         assert st == blcoc.BLCOC_OK, lib.blcoc_last_error(None)
         torch.cuda.synchronize()
         values.append(float(out.item()))
+    assert torch.cuda.mem_get_info()[0] == free_before   # no device memory taken by the calls
     for v in values:
         assert abs(v - ref) <= RTOL * ref, (v, ref)
+        assert abs(v - ref_host) <= RTOL * ref_host, (v, ref_host)
     assert values[0] == values[1]          # fixed-order reduction: the same bits every call
 
 
