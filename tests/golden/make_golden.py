@@ -11,7 +11,14 @@ problem (n = 262,144, p = 16, tol 1e-10; several minutes on a CPU) and writes
 tests/golden/helmholtz3d_n262144_p16.json (status, iteration count, true relative
 residual and the whole recursive history).
 
-Run:  python tests/golden/make_golden.py [--full3d]
+With --quad3d it runs the first 20 iterations of bl_cocr_rq on the same 64^3 problem twice
+with oracle/blcoc_oracle_xp.py, in complex128 and in numpy.clongdouble (80-bit extended on
+x86, binary128 on aarch64; tens of minutes), and writes
+tests/golden/helmholtz3d_n262144_p16_extended.json: both histories and the FP64 run's
+relative deviation from the extended one at every m (the FP64 rounding floor of a
+residual-history comparison on this problem).
+
+Run:  python tests/golden/make_golden.py [--full3d] [--quad3d]
 """
 import json
 import os
@@ -47,7 +54,28 @@ def full3d():
         json.dump(out, fh, indent=0)
 
 
+def quad3d(iters=20):
+    import platform
+
+    import numpy as np
+    import oracle.blcoc_oracle_xp as XP
+    pr = P.helmholtz3d_n262144_p16("cocr_rq")
+    h64, _, _ = XP.bl_cocr_rq_xp(pr.A, pr.B, iters, np.complex128)
+    hx, _, _ = XP.bl_cocr_rq_xp(pr.A, pr.B, iters, XP.EXTENDED)
+    hx = [float(v) for v in hx]
+    dev = [abs(a - b) / b for a, b in zip(h64, hx)]
+    out = {"source": "oracle/blcoc_oracle_xp.py bl_cocr_rq_xp (Algorithm 3, Sec. 2.2)", "problem": pr.name,
+           "iters": iters, "extended": f"numpy.clongdouble on {platform.machine()}, eps "
+                                       f"{float(np.finfo(np.longdouble).eps):.3g}",
+           "hist_fp64": [float(v) for v in h64], "hist_extended": hx, "fp64_rel_dev": dev}
+    with open(os.path.join(HERE, "helmholtz3d_n262144_p16_extended.json"), "w") as fh:
+        json.dump(out, fh, indent=0)
+
+
 if __name__ == "__main__":
-    main()
+    if "--quad3d" not in sys.argv or "--full3d" in sys.argv:
+        main()
     if "--full3d" in sys.argv:
         full3d()
+    if "--quad3d" in sys.argv:
+        quad3d()
