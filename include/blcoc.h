@@ -220,12 +220,14 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  product per iteration instead of Algorithm 3's recurrence
  *                  U_{m+1} = V_{m+1} + U_m beta'_m (equal in exact arithmetic; the
  *                  recurrence is the default, 0).
- *   "fp64_tc"    : BLCOC_COCR_RQ with p <= 16: 1 runs the p x p block updates (right-
- *                  multiplications by alpha', alpha'xi, beta', tau^{-1}) on the bf16 tensor
- *                  cores by exact integer slicing of both operands (eight 7-bit digits,
- *                  43 slice products, exact fp32 partial sums), to about FP64 accuracy;
- *                  the Grams, the sparse product and the p x p stages stay FP64.  0 (default)
- *                  computes them with FP64 FMAs.
+ *   "fp64_tc"    : BLCOC_COCR_RQ and BLCOC_COCG_RQ with 5 <= p <= 32: 1 runs the p x p
+ *                  block updates (right-multiplications by alpha', alpha'xi, beta',
+ *                  tau^{-1}) on the bf16 tensor cores by exact integer slicing of both
+ *                  operands (eight 7-bit digits, 43 slice products, exact fp32 partial
+ *                  sums), to about FP64 accuracy; for BLCOC_COCR_RQ with p <= 16 the Grams
+ *                  W^H W and W^T A W as well.  The other Grams, the sparse product and the
+ *                  p x p stages stay FP64.  0 (default) computes everything with FP64 FMAs
+ *                  (so do p <= 4, the plain methods and the complex64 inner solves).
  *   "u_explicit_mixed": the same for the complex64 inner solves of BLCOC_COCR_RQ_MIXED
  *                  (default 1: the recurrence drifts quickly in single precision).
  *   "qr_passes"  : rq methods: 1 (default) forms the thin QR of W (Sec. 2.2, Q^H Q = I)
@@ -297,6 +299,18 @@ blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value);
 blcoc_status blcoc_residual_norm_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
                                          const void* vals, const void* B, const void* X, int p,
                                          double* norm_out, void* cuda_stream);
+
+/*
+ * blcoc_probe_peak - measured FMA throughput of the current device, in flop/s (an FMA
+ * counts as 2), for the ALU roofline the row passes are reported against.
+ *   kind        : 0 = FP64 (DFMA), 1 = FP32 (FFMA).
+ *   flops_per_s : receives the best of three timed launches (after one warm-up) of a
+ *                 kernel in which every resident thread runs eight independent FMA chains.
+ * Takes about 0.2 s; allocates 8 bytes of device memory and a stream for the call.
+ * The paper has no counterpart (a measuring utility).  Errors: BLCOC_ERR_INVALID_ARG,
+ * BLCOC_ERR_CUDA / BLCOC_ERR_OOM (message in blcoc_last_error(NULL)).
+ */
+blcoc_status blcoc_probe_peak(int kind, double* flops_per_s);
 
 /* blcoc_destroy - free the handle and everything it owns.  NULL is accepted. */
 blcoc_status blcoc_destroy(blcoc_handle h);

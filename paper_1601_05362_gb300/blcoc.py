@@ -54,6 +54,7 @@ SIGNATURES = {
                                       C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "blcoc_solve_batched_persistent": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                                  C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "blcoc_probe_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
     "blcoc_destroy": (C.c_int, [C.c_void_p]),
     "blcoc_status_string": (C.c_char_p, [C.c_int]),
     "blcoc_last_error": (C.c_char_p, [C.c_void_p]),
@@ -304,6 +305,17 @@ def solve_batched(handles, Bs, Xs, method="cocr_rq", tol=1e-10, maxit=None, auto
     if st not in (BLCOC_OK, BLCOC_NOT_CONVERGED, BLCOC_BREAKDOWN):
         raise BlcocError(st, msg or lib.blcoc_last_error(None).decode())
     return st, ms.value, msg
+
+
+def probe_peak(kind: str = "fp64") -> float:
+    """blcoc_probe_peak: measured FMA throughput of the current device in flop/s
+    (kind "fp64" or "fp32")."""
+    lib = load_library()
+    v = C.c_double()
+    st = lib.blcoc_probe_peak({"fp64": 0, "fp32": 1}[kind], C.byref(v))
+    if st != BLCOC_OK:
+        raise BlcocError(st, lib.blcoc_last_error(None).decode())
+    return v.value
 
 
 # ------------------------------------------------------------------ same names as the ABI

@@ -46,6 +46,13 @@ const KernelSet* kernels_for(int p, int* PP, bool f32 = false) {
   return f32 ? &kernel_set<32, float>() : &kernel_set<32, double>();
 }
 
+// Kernel set whose p x p block updates run on the tensor cores (block widths 8, 16, 32).
+const KernelSet* tc_kernels(int PP) {
+  if (PP == 8) return &kernel_set_tc<8>();
+  if (PP == 16) return &kernel_set_tc<16>();
+  return &kernel_set_tc<32>();
+}
+
 __global__ void k_vals_to_c64(const double2* __restrict__ v, float2* __restrict__ o, int64_t nnz) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x)
     o[i] = make_float2((float)v[i].x, (float)v[i].y);
@@ -1297,10 +1304,10 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   const int base_method = plain ? (method == BLCOC_COCR ? BLCOC_COCR_RQ : BLCOC_COCG_RQ) : (int)method;
   int PP = 0;
   Solver sv{h, kernels_for(p, &PP), PP, p, base_method, dB, dX};
-  const bool tc = h->fp64_tc && !plain && base_method == BLCOC_COCR_RQ && (PP == 8 || PP == 16);
+  const bool tc = h->fp64_tc && !plain && PP >= 8;
   if (tc) {
     if (!h->ozbuf) CK(h, cudaMalloc(&h->ozbuf, (size_t)OZ_NSLOTS * OZ_SLOT_U2 * sizeof(uint2)));
-    sv.K = PP == 8 ? &kernel_set_tc<8>() : &kernel_set_tc<16>();
+    sv.K = tc_kernels(PP);
     sv.oz = h->ozbuf;
   }
   sv.K->prepare();
@@ -1419,9 +1426,9 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     int PP = 0;
     sv.push_back(Solver{h, kernels_for(p[i], &PP), PP, p[i], (int)method, (const double2*)B[i], (double2*)X[i]});
     // per-system options, as in blcoc_solve: tensor-core block updates, explicit U, CholQR2
-    if (form == 0 && h->fp64_tc && method == BLCOC_COCR_RQ && (PP == 8 || PP == 16)) {
+    if (form == 0 && h->fp64_tc && PP >= 8) {
       if (!h->ozbuf) CK(h, cudaMalloc(&h->ozbuf, (size_t)OZ_NSLOTS * OZ_SLOT_U2 * sizeof(uint2)));
-      sv.back().K = PP == 8 ? &kernel_set_tc<8>() : &kernel_set_tc<16>();
+      sv.back().K = tc_kernels(PP);
       sv.back().oz = h->ozbuf;
     }
     sv.back().K->prepare();

@@ -8,14 +8,17 @@
 // column of M' by 2^f; each value becomes a 56-bit fixed-point magnitude cut into eight
 // 7-bit digits (sign kept), digit s weighted 2^(e - 7 s).  A digit (<= 127) is exact in
 // bf16, a digit product (< 2^14) is exact in fp32, and a level L = s + t sums at most 8
-// slice pairs over K <= 32 terms: < 2^23, still exact in the fp32 accumulator.  Levels
+// slice pairs over K <= 64 terms: 8 * 64 * 127^2 < 2^23, still exact in the fp32
+// accumulator.  Levels
 // 2..10 are kept (43 slice products); the dropped levels and the 56-bit cut contribute
 // about 2^-54 of |X'| |M'|, the size of FP64's own rounding in a K-term dot product.
 // Recombination: the nine exact level sums are combined as two 64-bit integers and turned
 // into a double with two conversions and two FMAs, added to the base value.
 //
 // The p x p stage kernels write each factor already split, in the B-fragment order of
-// mma.m16n8k16 (`oz_emit_factor`); the row passes split X' in registers (`oz_apply`).
+// mma.m16n8k16 (`oz_emit_factor`); the row passes split X' in registers (`oz_apply`,
+// p <= 16) or, at p = 32 where eight slices of four k16 steps would not fit in registers,
+// into a per-warp shared-memory buffer one 16-row tile at a time (`oz_apply_sm`).
 #pragma once
 
 #include "blcoc_common.cuh"
@@ -23,13 +26,15 @@
 namespace blcoc {
 
 // per-factor slot in the handle's slice buffer: fragments of the largest supported width
-// (p <= 16) followed by the 2p column exponents
-constexpr int OZ_SLOT_U2 = 8 * 2 * 4 * 32 + 32;   // uint2 units (16 KB + 256 B)
+// (p <= 32: 8 slices x 4 k16 steps x 8 n8 tiles x 32 lanes) followed by the 2p column
+// exponents
+constexpr int OZ_FRAG_MAX = 8 * 4 * 8 * 32;         // uint2 units (64 KB)
+constexpr int OZ_SLOT_U2 = OZ_FRAG_MAX + 32;        // + 64 ints of column exponents
 enum OzSlot { OZ_T = 0, OZ_ALPHA, OZ_ALPHAXI, OZ_BETA, OZ_NSLOTS };
 __host__ __device__ inline const int* oz_colexp_of(const uint2* slot) {
-  return reinterpret_cast<const int*>(slot + 8 * 2 * 4 * 32);
+  return reinterpret_cast<const int*>(slot + OZ_FRAG_MAX);
 }
-__host__ __device__ inline int* oz_colexp_of(uint2* slot) { return reinterpret_cast<int*>(slot + 8 * 2 * 4 * 32); }
+__host__ __device__ inline int* oz_colexp_of(uint2* slot) { return reinterpret_cast<int*>(slot + OZ_FRAG_MAX); }
 
 constexpr int OZ_NSL = 8;    // digits per value
 constexpr int OZ_DB = 7;     // bits per digit
@@ -130,6 +135,44 @@ __device__ __forceinline__ void oz_mma(float (&c)[4], const unsigned (&a)[4], ui
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
+// Recombination of the four outputs one lane holds for n-tile nt of an m-tile
+// ((ra, 8nt+2q), (ra, 8nt+2q+1), (rb, 8nt+2q), (rb, 8nt+2q+1)) from their nine exact level
+// sums, and their write to `out` (added to / subtracted from `base`).
+template <int PP, bool SUB, bool BASE>
+__device__ __forceinline__ void oz_store_outputs(double2* out, const double2* base, const float (&acc)[OZ_NLEV][4],
+                                                 const int* __restrict__ colexp, int ra, int rb, int eba, int ebb,
+                                                 int nt, int q, int p) {
+  auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int L = 2; L <= 6; ++L) hi += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (6 - L));
+#pragma unroll
+    for (int L = 7; L <= OZ_LMAX; ++L) lo += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (10 - L));
+    const int row = (o < 2) ? ra : rb;
+    const int col = 8 * nt + 2 * q + (o & 1);
+    const int ebr = (o < 2) ? eba : ebb;
+    const int ebc = __ldg(colexp + col);
+    // value = (hi 2^-42 + lo 2^-70) 2^(e_r + f_c), e = eb - 1022
+    const int sc = (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022) - 42;
+    double v = fma((double)lo, 0x1p-28, (double)hi);
+    if (ebr == 2047 || ebc == 2047) v = __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
+    else if (sc >= -1020 && sc <= 1020) v *= __longlong_as_double((long long)(sc + 1023) << 52);
+    else v = ldexp(v, sc);
+    const int kc = col % PP;
+    if (kc < p) {
+      double2 cur = BASE ? base[tx(kc, row)] : make_double2(0.0, 0.0);
+      double& dst = (col >= PP) ? cur.y : cur.x;
+      dst = SUB ? dst - v : dst + v;
+      // the real and imaginary halves of one complex output are written by different
+      // lanes (n-tiles nt and nt + NT/2): write only this lane's half
+      if (col >= PP) out[tx(kc, row)].y = cur.y;
+      else out[tx(kc, row)].x = cur.x;
+    }
+  }
+}
+
 // out = base (+/-) in * M for the warp's 32-row chunk (swizzled [k][32] tiles of double2,
 // columns >= p of `in` are ignored).  `out` may alias `base` or, without a base, `in`.
 // frag / colexp: the factor as written by oz_emit_factor (global memory).
@@ -206,36 +249,95 @@ __device__ __forceinline__ void oz_apply(double2* out, const double2* base, cons
           for (int ks = 0; ks < G::KS; ++ks) oz_mma(acc[s + t - 2], A[s - 1][ks], Bf[t - 1][ks]);
         }
       }
-      // recombination of the four outputs held by this lane:
-      // (ra, 8nt+2q), (ra, 8nt+2q+1), (rb, 8nt+2q), (rb, 8nt+2q+1)
+      oz_store_outputs<PP, SUB, BASE>(out, base, acc, colexp, ra, rb, eba, ebb, nt, q, p);
+    }
+  }
+}
+
+// Digit fragments of the A operand (X' rows ra = 16 mt + g and rb = ra + 8, real columns
+// 16 ks + {2q, 2q+1, 2q+8, 2q+9}) of one 16-row tile, written to the warp's buffer
+// adig[(t * KS + ks) * 32 + lane] (uint4: the four A registers of slice t, k-step ks).
+template <int PP>
+__device__ __forceinline__ void oz_split_rows_to_smem(uint4* adig, const double2* in, int p, int ra, int rb, int eba,
+                                                      int ebb, int lane) {
+  using G = OzGeo<PP>;
+  auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
+  const int q = lane & 3;
+#pragma unroll 1
+  for (int ks = 0; ks < G::KS; ++ks) {
+    unsigned long long F[8];
+    unsigned sg[8];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        long long hi = 0, lo = 0;
+    for (int c = 0; c < 4; ++c) {
+      const int col = 16 * ks + 2 * q + (c & 1) + 8 * (c >> 1);
+      const int kc = col % PP;
+      const bool im = col >= PP;
+      double va = 0.0, vb = 0.0;
+      if (kc < p) {
+        const double2 xa = in[tx(kc, ra)], xb = in[tx(kc, rb)];
+        va = im ? xa.y : xa.x;
+        vb = im ? xb.y : xb.x;
+      }
+      F[2 * c] = oz_fixed(va, eba);
+      sg[2 * c] = (__double_as_longlong(va) < 0) ? 1u : 0u;
+      F[2 * c + 1] = oz_fixed(vb, ebb);
+      sg[2 * c + 1] = (__double_as_longlong(vb) < 0) ? 1u : 0u;
+    }
 #pragma unroll
-        for (int L = 2; L <= 6; ++L) hi += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (6 - L));
+    for (int t = 0; t < OZ_NSL; ++t) {
+      const int shft = 56 - OZ_DB * (t + 1);
+      unsigned h[8];
 #pragma unroll
-        for (int L = 7; L <= OZ_LMAX; ++L) lo += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (10 - L));
-        const int row = (o < 2) ? ra : rb;
-        const int col = 8 * nt + 2 * q + (o & 1);
-        const int ebr = (o < 2) ? eba : ebb;
-        const int ebc = __ldg(colexp + col);
-        // value = (hi 2^-42 + lo 2^-70) 2^(e_r + f_c), e = eb - 1022
-        const int sc = (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022) - 42;
-        double v = fma((double)lo, 0x1p-28, (double)hi);
-        if (ebr == 2047 || ebc == 2047) v = __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
-        else if (sc >= -1020 && sc <= 1020) v *= __longlong_as_double((long long)(sc + 1023) << 52);
-        else v = ldexp(v, sc);
-        const int kc = col % PP;
-        if (kc < p) {
-          double2 cur = BASE ? base[tx(kc, row)] : make_double2(0.0, 0.0);
-          double& dst = (col >= PP) ? cur.y : cur.x;
-          dst = SUB ? dst - v : dst + v;
-          // the real and imaginary halves of one complex output are written by different
-          // lanes (n-tiles nt and nt + NT/2): write only this lane's half
-          if (col >= PP) out[tx(kc, row)].y = cur.y;
-          else out[tx(kc, row)].x = cur.x;
+      for (int e = 0; e < 8; ++e) h[e] = oz_bf16((unsigned)((F[e] >> shft) & 127ull), sg[e]);
+      adig[(t * G::KS + ks) * 32 + lane] =
+          make_uint4(h[0] | (h[2] << 16), h[1] | (h[3] << 16), h[4] | (h[6] << 16), h[5] | (h[7] << 16));
+    }
+  }
+}
+
+// oz_apply with the A digits staged in shared memory (p = 32): `adig` is this warp's
+// buffer of OZ_NSL * KS * 32 uint4 (16 KB at p = 32).  Same arithmetic, same results.
+template <int PP, bool SUB, bool BASE>
+__device__ __forceinline__ void oz_apply_sm(double2* out, const double2* base, const double2* in,
+                                            const uint2* __restrict__ frag, const int* __restrict__ colexp, int p,
+                                            int lane, uint4* adig) {
+  using G = OzGeo<PP>;
+  auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
+  int eb_row = 0;
+  for (int k = 0; k < p; ++k) {
+    const double2 v = in[tx(k, lane)];
+    eb_row = max(eb_row, max(oz_bexp(v.x), oz_bexp(v.y)));
+  }
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll 1
+  for (int mt = 0; mt < 2; ++mt) {
+    const int ra = 16 * mt + g, rb = ra + 8;
+    const int eba = __shfl_sync(0xffffffffu, eb_row, ra), ebb = __shfl_sync(0xffffffffu, eb_row, rb);
+    __syncwarp();   // the previous tile's digits have been read
+    oz_split_rows_to_smem<PP>(adig, in, p, ra, rb, eba, ebb, lane);
+    __syncwarp();
+#pragma unroll 1
+    for (int nt = 0; nt < G::NT; ++nt) {
+      float acc[OZ_NLEV][4];
+#pragma unroll
+      for (int l = 0; l < OZ_NLEV; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.f;
+#pragma unroll 1
+      for (int ks = 0; ks < G::KS; ++ks) {
+        uint2 Bf[OZ_NSL];
+#pragma unroll
+        for (int t = 0; t < OZ_NSL; ++t) Bf[t] = __ldg(frag + (t * G::KS + ks) * G::NT * 32 + nt * 32 + lane);
+#pragma unroll
+        for (int s = 1; s <= OZ_NSL; ++s) {
+          const uint4 a4 = adig[((s - 1) * G::KS + ks) * 32 + lane];
+          const unsigned A[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+          for (int t = 1; t <= OZ_NSL; ++t) {
+            if (s + t > OZ_LMAX) continue;
+            oz_mma(acc[s + t - 2], A, Bf[t - 1]);
+          }
         }
       }
+      oz_store_outputs<PP, SUB, BASE>(out, base, acc, colexp, ra, rb, eba, ebb, nt, q, p);
     }
   }
 }

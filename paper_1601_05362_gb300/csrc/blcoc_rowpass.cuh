@@ -20,6 +20,8 @@
 // shared-memory bank conflicts.
 #pragma once
 
+#include <type_traits>
+
 #include "blcoc_common.cuh"
 #include "blcoc_ozaki.cuh"
 
@@ -38,12 +40,23 @@ struct Geo {
 
 __device__ __forceinline__ int tix(int k, int r) { return k * CHUNK + (r ^ (k & 7)); }
 
+// Parts a staged p x p factor is kept in: FP64 one; complex64 two, hi = fl(M) and
+// lo = fl(M - hi), so that a complex64 row pass applies the FP64 factor to about 2^-48
+// relative accuracy instead of rounding it to 2^-24.  (Rounding the factors is not
+// harmless: every row of the block then moves by the same relative error, which on
+// indefinite problems destroys the bilinear orthogonality of Table 1 within a few dozen
+// iterations.)
+template <typename S>
+constexpr int mat_parts() { return sizeof(S) == 4 ? 2 : 1; }
+
 // Elements taken by nm staged p x p factors, rounded up to a 16-byte boundary so that the
 // tiles (and the FP64 reduction area that reuses them) stay 16-byte aligned.
 template <int PP, typename S>
 constexpr int mats_off(int nm) {
   using C = typename Cx<S>::T;
-  return Geo<PP, S>::MATS_SMEM ? (int)((((size_t)nm * PP * PP * sizeof(C) + 15) / 16 * 16) / sizeof(C)) : 0;
+  return Geo<PP, S>::MATS_SMEM
+             ? (int)((((size_t)nm * mat_parts<S>() * PP * PP * sizeof(C) + 15) / 16 * 16) / sizeof(C))
+             : 0;
 }
 
 // ---------------------------------------------------------------------------------- tiles
@@ -85,46 +98,77 @@ __device__ __forceinline__ void store_tile_f32(float2* __restrict__ g, const dou
   }
 }
 
+// A factor entry of the complex64 passes: hi + lo (see mat_parts).
+struct f2pair {
+  float2 hi, lo;
+};
+// acc += y (hi + lo), acc -= y (hi + lo): the small part first, then the large one.
+__device__ __forceinline__ void cmac(float2& acc, float2 y, f2pair m) {
+  cmac(acc, y, m.lo);
+  cmac(acc, y, m.hi);
+}
+__device__ __forceinline__ void cmsub(float2& acc, float2 y, f2pair m) {
+  cmsub(acc, y, m.lo);
+  cmsub(acc, y, m.hi);
+}
+
+// Write FP64 factor entry v at index i of a staged factor whose parts are `stride`
+// elements apart (one part for FP64, hi and lo for complex64).
+__device__ __forceinline__ void put_fac(double2* s, int i, int, double2 v) { s[i] = v; }
+__device__ __forceinline__ void put_fac(float2* s, int i, int stride, double2 v) {
+  const float2 hi = make_float2((float)v.x, (float)v.y);
+  s[i] = hi;
+  s[stride + i] = make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
+}
+
 // Stage a p x p FP64 factor (row stride p in global) as PP x PP in the working precision,
-// zero padded.
+// zero padded (complex64: hi part, then lo part PP*PP elements further).
 template <int PP, typename C>
 __device__ __forceinline__ void load_mat(C* s, const double2* __restrict__ g, int p) {
   for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
     const int k = e / PP, j = e - k * PP;
-    s[e] = (k < p && j < p) ? from_d2<C>(BLCOC_LD(g + k * p + j)) : czero<C>();
+    put_fac(s, e, PP * PP, (k < p && j < p) ? BLCOC_LD(g + k * p + j) : cz());
   }
 }
 
 // Factor access: shared memory (stride PP) or, for FP64 at PP = 32, global memory
-// through the read-only path (row stride p).
+// through the read-only path (row stride p).  complex64: the hi + lo pair.
 template <int PP, typename S>
 struct Fac {
   using C = typename Cx<S>::T;
   const C* m;
   int ld;
-  __device__ __forceinline__ C operator()(int k, int j) const {
-    if constexpr (Geo<PP, S>::MATS_SMEM) return m[k * PP + j];
+  __device__ __forceinline__ auto operator()(int k, int j) const {
+    if constexpr (sizeof(S) == 4) return f2pair{m[k * PP + j], m[PP * PP + k * PP + j]};
+    else if constexpr (Geo<PP, S>::MATS_SMEM) return m[k * PP + j];
     else return __ldg(m + k * ld + j);
   }
 };
 
+template <int PP>
+constexpr int tri_packed() { return PP * (PP + 1) / 2; }
+
 // Upper-triangular factor packed row by row in shared memory (row k holds columns k..PP-1);
-// only entries with j >= k are read.
+// only entries with j >= k are read.  complex64: the hi + lo pair.
 template <int PP, typename S>
 struct FacTri {
   using C = typename Cx<S>::T;
   const C* m;
-  __device__ __forceinline__ C operator()(int k, int j) const { return m[k * PP - (k * (k - 1)) / 2 + (j - k)]; }
+  __device__ __forceinline__ auto operator()(int k, int j) const {
+    const int i = k * PP - (k * (k - 1)) / 2 + (j - k);
+    if constexpr (sizeof(S) == 4) return f2pair{m[i], m[tri_packed<PP>() + i]};
+    else return m[i];
+  }
 };
-template <int PP>
-constexpr int tri_packed() { return PP * (PP + 1) / 2; }
 
-// Stage the upper triangle of a p x p FP64 factor, packed (zero outside p).
+// Stage the upper triangle of a p x p FP64 factor, packed (zero outside p; complex64: hi
+// part, then lo part tri_packed elements further).
 template <int PP, typename C>
 __device__ __forceinline__ void load_mat_tri(C* s, const double2* __restrict__ g, int p) {
   for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
     const int k = e / PP, j = e - k * PP;
-    if (j >= k) s[k * PP - (k * (k - 1)) / 2 + (j - k)] = (k < p && j < p) ? from_d2<C>(BLCOC_LD(g + k * p + j)) : czero<C>();
+    if (j >= k)
+      put_fac(s, k * PP - (k * (k - 1)) / 2 + (j - k), tri_packed<PP>(), (k < p && j < p) ? BLCOC_LD(g + k * p + j) : cz());
   }
 }
 
@@ -134,7 +178,8 @@ template <int PP, typename S>
 constexpr int passC_mats_elems() {
   using C = typename Cx<S>::T;
   return Geo<PP, S>::MATS_SMEM
-             ? (int)((((size_t)(tri_packed<PP>() + 2 * PP * PP) * sizeof(C) + 15) / 16 * 16) / sizeof(C))
+             ? (int)((((size_t)(tri_packed<PP>() + 2 * PP * PP) * mat_parts<S>() * sizeof(C) + 15) / 16 * 16) /
+                     sizeof(C))
              : 0;
 }
 
@@ -205,6 +250,24 @@ __device__ __forceinline__ void apply_full(typename Cx<S>::T* out, const typenam
 // relative to |y| |M| (the terms are bounded by (|a| + |b|)(|c| + |d|) <= 2 |y| |M|).
 template <int PP, typename S, bool OZ = false>
 constexpr bool m3_apply() { return sizeof(S) == 8 && !OZ && PP >= 8; }
+// Tensor-core Grams (exact slices, per-warp FP64 sums in shared memory) are built for
+// p <= 16; at p = 32 the tensor-core passes keep their Grams on the FP64 pipe (the sums
+// of 64 x 64 real entries per warp would not fit beside the tiles).
+template <int PP, bool OZ>
+constexpr bool oz_gram() { return OZ && PP <= 16; }
+
+// Per-warp shared-memory buffer of the p = 32 tensor-core applies (A digit fragments of
+// one 16-row tile), in uint4 units; 0 where the applies split in registers.
+template <int PP, bool OZ>
+constexpr int oz_adig_u4() { return (OZ && PP >= 32) ? OZ_NSL * OzGeo<PP>::KS * 32 : 0; }
+
+// out = base (+/-) in * M on the tensor cores, M given by its exact-slice fragments.
+template <int PP, bool SUB, bool BASE>
+__device__ __forceinline__ void oz_apply_any(double2* out, const double2* base, const double2* in, const uint2* fz,
+                                             int p, int lane, uint4* adig) {
+  if constexpr (PP >= 32) oz_apply_sm<PP, SUB, BASE>(out, base, in, fz, oz_colexp_of(fz), p, lane, adig);
+  else oz_apply<PP, SUB, BASE>(out, base, in, fz, oz_colexp_of(fz), p, lane);
+}
 template <int PP, typename S>
 constexpr bool m3_gram() { return sizeof(S) == 8 && PP >= 8; }
 
@@ -308,6 +371,30 @@ __device__ __forceinline__ void sd_tile(double2* sd, const double2* t, int p, in
 // ---------------------------------------------------------------------------------- grams
 enum GramKind { G_FULL = 0, G_SYM = 1, G_HERM = 2 };
 
+// Double-float accumulator of a complex Gram entry (complex64 passes, unconjugated Grams).
+struct DF2 {
+  float2 hi, lo;
+};
+// hi + lo += a b with the product taken exactly (fma gives its rounding error) and the
+// sum's rounding error kept (Knuth's two-sum); explicit _rn operations so the compiler
+// neither contracts nor reorders them.
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
+  const float pr = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -pr);
+  const float s = __fadd_rn(hi, pr);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(pr, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, pe));
+}
+// d += y z (unconjugated), every real product exact and every sum compensated.
+__device__ __forceinline__ void df_cmac(DF2& d, float2 y, float2 z) {
+  df_add_prod(d.hi.x, d.lo.x, y.x, z.x);
+  df_add_prod(d.hi.x, d.lo.x, -y.y, z.y);
+  df_add_prod(d.hi.y, d.lo.y, y.x, z.y);
+  df_add_prod(d.hi.y, d.lo.y, y.y, z.x);
+}
+
 template <int NS, typename S, bool M3 = false>
 struct GramAcc {
   // Entries e = lane + 32 i (i < F) take all 32 rows of a chunk.  The Er = E mod 32
@@ -358,7 +445,8 @@ struct GramAcc {
   __device__ __forceinline__ void mac(A& dst, int i, const C* Y, const C* Z, int r) const {
     const C y = Y[tix(a[i], r)];
     const C z = Z[tix(b[i], r)];
-    if constexpr (CONJ) cmac_conj(dst, y, z);
+    if constexpr (std::is_same<A, DF2>::value) df_cmac(dst, y, z);
+    else if constexpr (CONJ) cmac_conj(dst, y, z);
     else cmac(dst, y, z);
   }
   template <bool CONJ, typename A>
@@ -386,11 +474,27 @@ struct GramAcc {
       }
     }
   }
-  // acc[e] += sum_r op(Y[r][a_e]) Z[r][b_e] over the 32 rows of a chunk
+  // acc[e] += sum_r op(Y[r][a_e]) Z[r][b_e] over the 32 rows of a chunk.
+  // complex64, unconjugated (the coefficient Grams of Table 1): every product of two
+  // complex64 entries is exact and the chunk sum is double-float, so the Gram is about as
+  // accurate as an FP64 sum of the stored values.  These bilinear forms cancel heavily
+  // (|Y^T Z| can be far below sum |y||z|); summed in plain FP32 their error stops the
+  // iteration on indefinite problems.  The Hermitian Gram of the Cholesky QR keeps the
+  // FP32 chunk sums (its terms do not cancel).
   template <bool CONJ>
   __device__ __forceinline__ void add(const C* Y, const C* Z, int lane) {
     if constexpr (sizeof(S) == 8) {
       add_rows<CONJ>(acc, Y, Z, lane);
+    } else if constexpr (!CONJ) {
+      DF2 part[NS];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) part[i] = DF2{czero<C>(), czero<C>()};
+      add_rows<false>(part, Y, Z, lane);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        acc[i].x += (double)part[i].hi.x + (double)part[i].lo.x;
+        acc[i].y += (double)part[i].hi.y + (double)part[i].lo.y;
+      }
     } else {
       C part[NS];
 #pragma unroll
@@ -646,8 +750,10 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   Fac<PP, S> T{G::MATS_SMEM ? T_s : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
   GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
+  constexpr bool OZG = oz_gram<PP, OZ>();
   double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
-  if constexpr (OZ) {
+  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
+  if constexpr (OZG) {
     for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
   }
   double dummy0 = 0.0, dummy1 = 0.0;
@@ -656,7 +762,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     gather_rows<PP, C, false, SPL>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
     load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
-    if constexpr (OZ) {
+    if constexpr (OZG) {
       if (a.flag & F_UEXPL) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tY, tY, p, lane);
       else oz_gram_add<PP, false>(zsums + warp * OzGramGeo<PP>::ACC, tW, tY, p, lane);
     } else {
@@ -665,8 +771,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     __syncwarp();   // every lane has read Y for the Gram before the in-place apply
     if (applyT) {
       if constexpr (OZ) {
-        const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
-        oz_apply<PP, false, false>(tY, nullptr, tY, fz, oz_colexp_of(fz), p, lane);
+        oz_apply_any<PP, false, false>(tY, nullptr, tY, a.oz + OZ_T * OZ_SLOT_U2, p, lane, adig);
       } else if constexpr (M3A) {
         tri_apply3_inplace<PP>(tY, Fac3(a.mats, M_TINV, p), p, lane);
       } else {
@@ -678,7 +783,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     __syncwarp();
   }
   __syncthreads();
-  if constexpr (OZ) oz_gram_write<PP, false>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
+  if constexpr (OZG) oz_gram_write<PP, false>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
   else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
 // Two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to that
@@ -717,7 +822,10 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
-  constexpr bool M3G = M3A;   // W^H W: three products where the applies take them (OZ: tensor cores)
+  constexpr bool OZG = oz_gram<PP, OZ>();
+  // W^H W: three products where the applies take them, and in the p = 32 tensor-core pass
+  // (whose Gram stays on the FP64 pipe); the p <= 16 tensor-core pass forms it there
+  constexpr bool M3G = M3A || (OZ && !OZG);
   C* mA = smem;
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
   C* tW = tiles + warp * 2 * G::TILE;
@@ -730,7 +838,8 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   GramAcc<G::NTRI, S, M3G> g;
   g.init(G_HERM, p, lane);
   double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
-  if constexpr (OZ) {
+  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
+  if constexpr (OZG) {
     for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
   }
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
@@ -739,8 +848,11 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
     load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
     if constexpr (OZ) {
-      const uint2* fz = a.oz + OZ_ALPHA * OZ_SLOT_U2;
-      oz_apply<PP, true, true>(tW, tW, tU, fz, oz_colexp_of(fz), p, lane);
+      oz_apply_any<PP, true, true>(tW, tW, tU, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane, adig);
+      if constexpr (M3G) {
+        __syncwarp();
+        sd_tile<PP>(tU, tW, p, lane);                                         // U_m is no longer needed
+      }
     } else if constexpr (M3A) {
       apply_full3<PP, true>(tW, tW, tU, Fac3(a.mats, M_ALPHA, p), p, lane);   // W_{m+1} = Q_m - U_m alpha'
       sd_tile<PP>(tU, tW, p, lane);                                           // U_m is no longer needed
@@ -748,14 +860,14 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
       apply_full<PP, S, true>(tW, tW, tU, AL, p, lane);    // W_{m+1} = Q_m - U_m alpha'
     }
     __syncwarp();
-    if constexpr (OZ) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tW, tW, p, lane);
+    if constexpr (OZG) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tW, tW, p, lane);
     else if constexpr (M3G) g.template add3<true>(tW, tU, lane);
     else g.template add<true>(tW, tW, lane);
     store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
     __syncwarp();
   }
   __syncthreads();
-  if constexpr (OZ) oz_gram_write<PP, true>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
+  if constexpr (OZG) oz_gram_write<PP, true>(zsums, a.partials + (int64_t)vblk * a.ne, p, NWARP);
   else cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
 // FP64: two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to
@@ -786,13 +898,14 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   constexpr bool M3G = m3_gram<PP, S>();
   // staged factors (four-product forms): T packed (upper triangle), alpha'xi, beta'
   C* mT = smem;
-  C* mAX = smem + tri_packed<PP>();
-  C* mB = mAX + PP * PP;
+  C* mAX = smem + tri_packed<PP>() * mat_parts<S>();
+  C* mB = mAX + PP * PP * mat_parts<S>();
   C* tiles = smem + (M3A ? 0 : passC_mats_elems<PP, S>());
   // two tiles per warp: Q is stored as soon as it is formed and read back (from L2, by the
   // same threads) for the S update, so X, S and Q never need three tiles at once
   C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
+  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
   if constexpr (G::MATS_SMEM && !M3A) {
     load_mat_tri<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
@@ -808,8 +921,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
     if constexpr (OZ) {
-      const uint2* fz = a.oz + OZ_T * OZ_SLOT_U2;
-      oz_apply<PP, false, false>(b0, nullptr, b0, fz, oz_colexp_of(fz), p, lane);
+      oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane, adig);
     } else if constexpr (M3A) {
       tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);       // Q_{m+1}
     } else if constexpr (G::MATS_SMEM) {
@@ -826,8 +938,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
       __syncwarp();
       if constexpr (OZ) {
-        const uint2* fz = a.oz + OZ_ALPHAXI * OZ_SLOT_U2;
-        oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
+        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane, adig);
       } else if constexpr (M3A) {
         apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_ALPHAXI, p), p, lane);   // X_{m+1}
       } else {
@@ -839,8 +950,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       load_tile<PP>(b0, blk<C>(a.Q), r0, n, p, lane);      // Q_{m+1}, just stored
       __syncwarp();
       if constexpr (OZ) {
-        const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
-        oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
+        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane, adig);
       } else if constexpr (M3A) {
         apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);      // S_{m+1} = Q + S beta'
       } else {
@@ -856,8 +966,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
     __syncwarp();
     if (!first) {
       if constexpr (OZ) {
-        const uint2* fz = a.oz + OZ_BETA * OZ_SLOT_U2;
-        oz_apply<PP, false, true>(b0, b0, b1, fz, oz_colexp_of(fz), p, lane);
+        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane, adig);
       } else if constexpr (M3A) {
         apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);      // U_{m+1} = V + U beta'
       } else {
@@ -883,10 +992,11 @@ template <int PP, typename S, bool OZ = false>
 __global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
   d_cocr_passC<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
-// The tensor-core pass C: its shared memory allows 3 CTAs per SM, and so does this bound
-// on its registers (otherwise about 238, 2 per SM).
+// The tensor-core pass C: up to p = 16 its shared memory allows 3 CTAs per SM, and so does
+// this bound on its registers (otherwise about 238, 2 per SM); at p = 32 shared memory
+// allows one.
 template <int PP>
-__global__ void __launch_bounds__(NWARP * 32, 3) k_cocr_passC_tc(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 3) k_cocr_passC_tc(const PassArgs a) {
   d_cocr_passC<PP, double, true>(a, blockIdx.x, gridDim.x);
 }
 
@@ -902,7 +1012,7 @@ __device__ __forceinline__ void d_cocg_pass1(const PassArgs& a, const int vblk, 
   constexpr bool M3A = m3_apply<PP, S>();
   constexpr bool M3G = m3_gram<PP, S>() && PP <= 16;   // two Grams of 17 slots at PP = 32: no room
   C* mAX = smem;
-  C* mA = smem + PP * PP;
+  C* mA = smem + PP * PP * mat_parts<S>();
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(2));
   C* b0 = tiles + warp * 3 * G::TILE;
   C* b1 = b0 + G::TILE;
@@ -954,6 +1064,94 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass1(const PassArgs a) {
   d_cocg_pass1<PP, S>(a, blockIdx.x, gridDim.x);
 }
 
+// bl_cocg_rq pass 1 with the p x p updates on the tensor cores (option fp64_tc): the same
+// results as d_cocg_pass1, in two tiles per warp (the Grams are taken from W before X is
+// updated, so the slice digits of p = 32 fit beside the tiles).  The self-Grams W^H W and
+// W^T W run in three real products from W and its companion tile up to p = 16, in four at
+// p = 32 (two three-product accumulators would not fit in registers there).
+template <int PP>
+__device__ __forceinline__ void d_cocg_pass1_tc(const PassArgs& a, const int vblk, const int vgrid) {
+  using C = double2;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, double>;
+  constexpr bool M3G = PP <= 16;
+  C* tiles = smem;   // no staged factors: the applies read slice fragments
+  C* b0 = tiles + warp * 2 * G::TILE;
+  C* b1 = b0 + G::TILE;
+  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, true>();
+  GramAcc<G::NTRI, double, M3G> gh, gs;
+  gh.init(G_HERM, p, lane);
+  gs.init(G_SYM, p, lane);
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(b0, a.Q, r0, n, p, lane);
+    load_tile<PP>(b1, a.V, r0, n, p, lane);
+    __syncwarp();
+    oz_apply_any<PP, true, true>(b0, b0, b1, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane, adig);   // W = Q - A S alpha'
+    __syncwarp();
+    if constexpr (M3G) {
+      sd_tile<PP>(b1, b0, p, lane);   // A S_m is no longer needed
+      __syncwarp();
+      gh.template add3<true>(b0, b1, lane);
+      gs.template add3<false>(b0, b1, lane);
+    } else {
+      gh.template add<true>(b0, b0, lane);
+      gs.template add<false>(b0, b0, lane);
+    }
+    store_tile<PP>(a.W, b0, r0, n, p, lane);
+    __syncwarp();
+    load_tile<PP>(b0, a.X, r0, n, p, lane);
+    load_tile<PP>(b1, a.S, r0, n, p, lane);
+    __syncwarp();
+    oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane, adig);   // X_{m+1}
+    __syncwarp();
+    store_tile<PP>(a.X, b0, r0, n, p, lane);
+    __syncwarp();
+  }
+  __syncthreads();
+  double2* out = a.partials + (int64_t)vblk * a.ne;
+  cta_write_gram(gh, reinterpret_cast<double2*>(tiles), out, warp, lane);
+  cta_write_gram(gs, reinterpret_cast<double2*>(tiles), out + tri_count(p), warp, lane);
+}
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 2) k_cocg_pass1_tc(const PassArgs a) {
+  d_cocg_pass1_tc<PP>(a, blockIdx.x, gridDim.x);
+}
+
+// bl_cocg_rq pass 2 on the tensor cores: Q_{m+1} = W_{m+1} T_{m+1} (stored), S_{m+1} =
+// Q_{m+1} + S_m beta'_m (setup, flag 1: S_0 = Q_0).
+template <int PP>
+__device__ __forceinline__ void d_cocg_pass2_tc(const PassArgs& a, const int vblk, const int vgrid) {
+  using C = double2;
+  BLCOC_PROLOGUE(C)
+  using G = Geo<PP, double>;
+  const bool first = a.flag & 1;
+  C* tiles = smem;
+  C* b0 = tiles + warp * 2 * G::TILE;
+  C* b1 = b0 + G::TILE;
+  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, true>();
+  for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
+    const int64_t r0 = c * CHUNK;
+    load_tile<PP>(b0, a.W, r0, n, p, lane);
+    if (!first) load_tile<PP>(b1, a.S, r0, n, p, lane);
+    __syncwarp();
+    oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane, adig);   // Q_{m+1}
+    __syncwarp();
+    store_tile<PP>(a.Q, b0, r0, n, p, lane);
+    if (!first) {
+      __syncwarp();
+      oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane, adig);   // S_{m+1}
+    }
+    __syncwarp();
+    store_tile<PP>(a.S, b0, r0, n, p, lane);
+    __syncwarp();
+  }
+}
+template <int PP>
+__global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2_tc(const PassArgs a) {
+  d_cocg_pass2_tc<PP>(a, blockIdx.x, gridDim.x);
+}
+
 // bl_cocg_rq pass 2 (Algorithm 2, the S update): Q_{m+1} = W_{m+1} T_{m+1} (stored for the next
 // pass 1), S_{m+1} = Q_{m+1} + S_m beta'_m.  flag=1 (setup): S_0 = Q_0 = W_0 T_0.
 template <int PP, typename S>
@@ -964,7 +1162,7 @@ __device__ __forceinline__ void d_cocg_pass2(const PassArgs& a, const int vblk, 
   const bool first = a.flag & 1;
   constexpr bool M3A = m3_apply<PP, S>();
   C* mT = smem;
-  C* mB = smem + PP * PP;
+  C* mB = smem + PP * PP * mat_parts<S>();
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(2));
   C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
@@ -1074,9 +1272,11 @@ constexpr size_t pass_smem(int kind) {
   if (kind == K_RESID) return (size_t)NWARP * PP * CHUNK * sizeof(double2);   // FP64 residual tile
   // three-product applies read their factors from global memory (L1); the CholQR2 pass
   // then keeps a second tile for the companion of its three-product Gram
-  const bool oz_kind = OZ && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C);
-  const bool m3 = m3_apply<PP, S>() && !oz_kind;
-  const int nt = (kind == K_QR2 && m3_gram<PP, S>()) ? 2 : ntiles[kind];
+  const bool oz_kind = OZ && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1 ||
+                              kind == K_COCG_2);
+  const bool oz_cocg = OZ && (kind == K_COCG_1 || kind == K_COCG_2);
+  const bool m3 = (m3_apply<PP, S>() && !oz_kind) || oz_cocg;   // oz_cocg: no staged factors either
+  const int nt = (kind == K_QR2 && m3_gram<PP, S>()) ? 2 : (oz_cocg ? 2 : ntiles[kind]);
   const size_t mats =
       m3 ? 0 : (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
   size_t s = mats + (size_t)NWARP * nt * tile;
@@ -1086,7 +1286,9 @@ constexpr size_t pass_smem(int kind) {
   const bool has_gram =
       kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1 || kind == K_QR2;
   if (has_gram && s < mats + red) s = mats + red;
-  if (OZ && (kind == K_COCR_A || kind == K_SPMM_GRAM)) s += (size_t)NWARP * OzGramGeo<PP>::ACC * sizeof(double);
+  if (oz_gram<PP, OZ>() && (kind == K_COCR_A || kind == K_SPMM_GRAM))
+    s += (size_t)NWARP * OzGramGeo<PP>::ACC * sizeof(double);
+  if (oz_kind) s += (size_t)NWARP * oz_adig_u4<PP, OZ>() * sizeof(uint4);   // p = 32: staged A digits
   return s;
 }
 
@@ -1103,8 +1305,12 @@ const void* pass_kernel(int kind) {
     case K_COCR_C:
       if constexpr (OZ) return (const void*)k_cocr_passC_tc<PP>;
       else return (const void*)k_cocr_passC<PP, S>;
-    case K_COCG_1: return (const void*)k_cocg_pass1<PP, S>;
-    case K_COCG_2: return (const void*)k_cocg_pass2<PP, S>;
+    case K_COCG_1:
+      if constexpr (OZ) return (const void*)k_cocg_pass1_tc<PP>;
+      else return (const void*)k_cocg_pass1<PP, S>;
+    case K_COCG_2:
+      if constexpr (OZ) return (const void*)k_cocg_pass2_tc<PP>;
+      else return (const void*)k_cocg_pass2<PP, S>;
     case K_QR2: return (const void*)k_qr2<PP, S>;
     default: return nullptr;
   }
@@ -1217,6 +1423,10 @@ void prepare_pass_kernels_tc() {
                        (int)pass_smem<PP, double, true>(K_COCR_A));
   cudaFuncSetAttribute(k_cocr_passC_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_C));
+  cudaFuncSetAttribute(k_cocg_pass1_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double, true>(K_COCG_1));
+  cudaFuncSetAttribute(k_cocg_pass2_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double, true>(K_COCG_2));
   set_spmm_split_smem<PP, double, true, 2>();
   set_spmm_split_smem<PP, double, true, 4>();
   done[dev] = true;
@@ -1230,8 +1440,8 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
       &launch_pass<PP, double, K_COCR_A, k_cocr_passA_tc<PP>, true>,
       &launch_pass<PP, double, K_COCR_C, k_cocr_passC_tc<PP>, true>,
-      &launch_pass<PP, double, K_COCG_1, k_cocg_pass1<PP, double>>,
-      &launch_pass<PP, double, K_COCG_2, k_cocg_pass2<PP, double>>,
+      &launch_pass<PP, double, K_COCG_1, k_cocg_pass1_tc<PP>, true>,
+      &launch_pass<PP, double, K_COCG_2, k_cocg_pass2_tc<PP>, true>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
       &launch_pass<PP, double, K_QR2, k_qr2<PP, double>>,
       spmm_split_fn<PP, double, true, 2>(),

@@ -145,13 +145,22 @@ __device__ double fro_norm(const double2* M, int p, double* red) {
 // Right-looking Cholesky of a Hermitian G (upper triangle used, destroyed): tau^H tau = G.
 // Per step warp 0 forms the pivot's inverse square root and row j of tau, then all threads
 // update the trailing triangle: two barriers per step.
+// Breakdown (returns false): a pivot that is not finite or not above 64 eps times G's
+// original diagonal entry, i.e. column j of the block keeps less than about 1.2e-7 of its
+// norm outside the span of the columns before it - below that a Cholesky QR cannot
+// resolve the column (its error grows like cond^2 eps), and the block has lost rank to
+// working accuracy.
 __device__ bool chol_upper(double2* G, double2* tau, int p, double* sh) {
   for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) tau[e] = cz();
   __syncthreads();
+  // warp 0: lane l keeps the original diagonal entry l (p <= 32); G's diagonal entry j is
+  // first changed by step j - 1's update, after every lane read it here
+  const double g0 = (threadIdx.x < 32 && (int)threadIdx.x < p) ? G[threadIdx.x * LD + threadIdx.x].x : 0.0;
   for (int j = 0; j < p; ++j) {
     if (threadIdx.x < 32) {
       const double d = G[j * LD + j].x;
-      const bool ok = d > 0.0 && isfinite(d);
+      const double g0j = __shfl_sync(0xffffffffu, g0, j);
+      const bool ok = d > 0x1p-46 * g0j && d > 0.0 && isfinite(d);
       if (ok) {
         const double ir = rsqrt(d);
         for (int i = j + 1 + threadIdx.x; i < p; i += 32) {
@@ -230,8 +239,9 @@ __device__ __forceinline__ double2 crecip_piv(double2 z) {
 }
 
 // Solve M Z = R in place (R <- Z), Gaussian elimination with partial pivoting; M is
-// destroyed.  Pivot: the largest max(|re|, |im|) in the column (piv_key; a pivot that is
-// zero to 15 bits or not finite is a breakdown).  Step k: warp 0 finds the pivot row
+// destroyed.  Pivot: the largest max(|re|, |im|) in the column (piv_key).  Breakdown: a
+// pivot that is not finite or not above 64 eps times the largest max(|re|, |im|) of M
+// (M is singular to working accuracy).  Step k: warp 0 finds the pivot row
 // while each of its lanes forms the reciprocal of its own candidate, then swaps rows k
 // and piv (columns >= k of M, all of R) and scales the new row k by the pivot's reciprocal
 // in one pass, a column per lane; all threads then subtract M_ik x row k from every row
@@ -242,6 +252,15 @@ __device__ __forceinline__ double2 crecip_piv(double2 z) {
 __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, int* ish, int* piv = nullptr,
                          double2* pinvs = nullptr) {
   const int lane = threadIdx.x & 31;
+  // breakdown threshold as a pivot key: the key of M's largest entry with its exponent
+  // lowered by 46 (64 eps = 2^-46); every warp-0 lane computes it
+  unsigned thr = 0u;
+  if (threadIdx.x < 32) {
+    unsigned mx = 0u;
+    for (int e = lane; e < p * p; e += 32) mx = max(mx, piv_key(M[(e / p) * LD + e % p], 31) & ~31u);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    thr = ((mx >> 20) & 0x7FFu) > 46u ? mx - (46u << 20) : 0u;
+  }
   for (int k = 0; k < p; ++k) {
     if (threadIdx.x < 32) {
       const bool cand = lane >= k && lane < p;
@@ -250,7 +269,7 @@ __device__ bool lu_solve(double2* M, double2* R, int p, int nrhs, double* sh, in
       const double2 zr = crecip_piv(cand ? z : make_double2(1.0, 0.0));
       const unsigned best = __reduce_max_sync(0xffffffffu, key);
       const int bi = 31 - (int)(best & 31u);
-      const bool ok = (best & ~31u) != 0u && ((best >> 20) & 0x7FFu) != 0x7FFu && bi >= k && bi < p;
+      const bool ok = (best & ~31u) > thr && ((best >> 20) & 0x7FFu) != 0x7FFu && bi >= k && bi < p;
       double2 pinv;
       pinv.x = __shfl_sync(0xffffffffu, zr.x, bi & 31);
       pinv.y = __shfl_sync(0xffffffffu, zr.y, bi & 31);
@@ -344,7 +363,8 @@ __device__ void emit_oz(uint2* oz, int slot, const double2* M, int p, int* sh) {
   if (oz == nullptr) return;
   uint2* f = oz + slot * OZ_SLOT_U2;
   if (p <= 8) oz_emit_factor<8>(M, LD, p, f, oz_colexp_of(f), sh);
-  else oz_emit_factor<16>(M, LD, p, f, oz_colexp_of(f), sh);
+  else if (p <= 16) oz_emit_factor<16>(M, LD, p, f, oz_colexp_of(f), sh);
+  else oz_emit_factor<32>(M, LD, p, f, oz_colexp_of(f), sh);
 }
 
 __device__ __forceinline__ double2* slot(double2* mats, int s) { return mats + s * PMAX * PMAX; }
@@ -562,6 +582,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
       return;
     }
     gstore_fac(mats, M_BETA, S.m[4], p);
+    emit_oz(oz, OZ_BETA, S.m[4], p, S.colexp);
   }
 }
 
@@ -611,6 +632,7 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
         return;
       }
       gstore_fac(mats, M_BETA, S.m[5], p);
+      emit_oz(oz, OZ_BETA, S.m[5], p, S.colexp);
     }
   }
   gstore_fac(mats, M_TINV, S.m[2], p);

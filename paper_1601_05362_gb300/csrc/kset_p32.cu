@@ -4,3 +4,6 @@ namespace blcoc {
 template const KernelSet& kernel_set<32, double>();
 template const KernelSet& kernel_set<32, float>();
 }
+namespace blcoc {
+template const KernelSet& kernel_set_tc<32>();
+}

@@ -122,3 +122,33 @@ def test_batched_honours_tensor_core_and_explicit_u_options():
         blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=5000, autotune=False, persistent=True)
     for h in hs:
         h.close()
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_batch_of_config_sized_systems_matches_oracle(persistent):
+    """Systems of the 64-system batch workload itself (2D Helmholtz, seed 3): the largest
+    grid sides it draws (up to 512, n up to 262,144) together with small ones, through
+    the CUDA-graph batch and the persistent kernel at a fixed iteration count, each system
+    against the oracle: history <= 1e-8 and X_m <= 1e-10 relative."""
+    torch = need_gpu()
+    import oracle.blcoc_oracle as O
+    from paper_1601_05362_gb300 import blcoc
+    from gpu_common import rel
+    allp = P.helmholtz2d_batch(64)
+    big = sorted(range(64), key=lambda i: -allp[i].n)[:3]
+    small = sorted(range(64), key=lambda i: allp[i].n)[:2]
+    pick = [allp[i] for i in big + small if allp[i].p <= 16]
+    m = 10
+    hs = [blcoc.Handle.from_csr(pr.A) for pr in pick]
+    Bs = [to_dev(torch, pr.B) for pr in pick]
+    Xs = [torch.zeros_like(B) for B in Bs]
+    st, _, _ = blcoc.solve_batched(hs, Bs, Xs, tol=0.0, maxit=m, autotune=False, persistent=persistent)
+    assert st == blcoc.BLCOC_NOT_CONVERGED
+    assert max(pr.extra["side"] for pr in pick) >= 500
+    for pr, h, X in zip(pick, hs, Xs):
+        ref = O.bl_cocr_rq(pr.A.to_scipy(), pr.B, tol=0.0, maxit=m)
+        info = h.info()
+        assert info["iters"] == m
+        assert np.max(np.abs(info["hist"] - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8, pr.name
+        assert rel(X.cpu().numpy(), ref.X) < 1e-10, pr.name
+        h.close()

@@ -103,6 +103,8 @@ def test_fp64_tc_first_iterations_and_solve(problem):
         X = torch.zeros_like(B)
         assert h.solve(B, X, tol=0.0, maxit=5) == blcoc.BLCOC_NOT_CONVERGED
         assert rel(X.cpu().numpy(), ref5.X) < 1e-10
+        xi5 = h.xi(pr.p)
+        assert np.max(np.abs(xi5 - ref5.xi)) / np.linalg.norm(ref5.xi) < 1e-10
         X.zero_()
         assert h.solve(B, X, tol=0.0, maxit=20) == blcoc.BLCOC_NOT_CONVERGED
         hist = np.asarray(h.info()["hist"])
@@ -142,3 +144,53 @@ def test_cholqr2_first_iterations_match_oracle(problem):
     herr = np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)
     assert np.max(herr[:11]) < 1e-8, herr        # m <= 10: before the amplification sets in
     assert np.max(herr) < max(1e-8, 10 * hsens), (np.max(herr), hsens)
+
+
+@pytest.fixture(scope="module")
+def problem128():
+    return P.helmholtz3d_n2097152_p32("cocr_rq")
+
+
+@pytest.fixture(scope="module")
+def oracle128_5(problem128):
+    """The oracle's 5 iterations, and its own sensitivity to a 1e-16 relative perturbation
+    of B (X_5 and xi_5; measured 9.2e-11 and 3.3e-11 on x86)."""
+    pr = problem128
+    A = pr.A.to_scipy()
+    ref = O.bl_cocr_rq(A, pr.B, tol=0.0, maxit=5)
+    Bp = pr.B * (1.0 + 1e-16 * np.random.default_rng(0).standard_normal(pr.B.shape))
+    rp = O.bl_cocr_rq(A, Bp, tol=0.0, maxit=5)
+    sens_x = rel(rp.X, ref.X)
+    sens_xi = float(np.max(np.abs(rp.xi - ref.xi)) / np.linalg.norm(ref.xi))
+    return ref, sens_x, sens_xi
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+def test_128cube_p32_first_iterations_match_oracle(problem128, oracle128_5, tc):
+    """The n >= 2M case at its full size (128^3 Helmholtz, k = 40, n = 2,097,152, p = 32,
+    nnz = 14.6M) in the launch configuration bench.py times: the FP64 path and the
+    tensor-core path (fp64_tc, block width 32) against the oracle after 5 iterations -
+    history <= 1e-8, X_5 and xi_5 elementwise within max(1e-10, 10x the oracle's own
+    sensitivity to a rounding-level perturbation of B): at this size a 1e-16 change of B
+    already moves the oracle's X_5 by about 1e-10, so two FP64 implementations that round
+    differently cannot be held closer."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    pr = problem128
+    ref, sens_x, sens_xi = oracle128_5
+    with blcoc.Handle.from_csr(pr.A) as h:
+        h.set_option("fp64_tc", tc)
+        B = to_dev(torch, pr.B)
+        X = torch.zeros_like(B)
+        assert h.solve(B, X, tol=0.0, maxit=5) == blcoc.BLCOC_NOT_CONVERGED
+        info = h.info()
+        xi = h.xi(pr.p)
+        Xh = X.cpu().numpy()
+        del X, B
+    hist = np.asarray(info["hist"])
+    assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8
+    assert rel(Xh, ref.X) < max(1e-10, 10 * sens_x), (rel(Xh, ref.X), sens_x)
+    dxi = np.max(np.abs(xi - ref.xi)) / np.linalg.norm(ref.xi)
+    assert dxi < max(1e-10, 10 * sens_xi), (dxi, sens_xi)
+    torch.cuda.empty_cache()
+

@@ -197,6 +197,37 @@ def test_edge_cases():
     assert st == blcoc.BLCOC_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
+@pytest.mark.parametrize("gap,expect", [(1e-15, "breakdown"), (1e-4, "ok")])
+def test_breakdown_on_nearly_dependent_columns_agrees_with_oracle(method, gap, expect):
+    """Right-hand sides whose last column equals the first up to a relative `gap`.  At
+    1e-15 the block has lost rank to working accuracy: the oracle's Householder factor has a
+    diagonal below 1e-14 of its largest and the GPU's Cholesky pivot is below 64 eps of the
+    column's squared norm, so both report a breakdown at the setup QR (rounding alone leaves
+    that pivot a tiny positive number, which a test on its sign lets through).  At 1e-4
+    neither does and the solve converges."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    A = P.random_complex_symmetric(600, 8, seed=41, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(A.n, 4, 42)
+    Bh[:, 3] = Bh[:, 0] * (1.0 + gap * P.complex_normal(A.n, 1, 43)[:, 0])
+    f = O.bl_cocg_rq if method == "cocg_rq" else O.bl_cocr_rq
+    ref = f(A.to_scipy(), Bh, tol=1e-10, maxit=500)
+    h = _handle(A)
+    B = to_dev(torch, Bh)
+    X = torch.zeros_like(B)
+    st = h.solve(B, X, method=method, tol=1e-10, maxit=500)
+    if expect == "breakdown":
+        assert ref.status == O.BREAKDOWN and ref.iters == 0
+        assert st == blcoc.BLCOC_BREAKDOWN and h.info()["iters"] == 0, blcoc.status_string(st)
+        assert float(X.abs().max()) == 0.0            # X_0 is returned unchanged
+    else:
+        assert ref.status == O.CONVERGED
+        assert st == blcoc.BLCOC_OK, h.last_error()
+        assert h.info()["relres_true"] <= 1e-9
+    h.close()
+
+
 def test_create_rejects_bad_matrices():
     need_gpu()
     from paper_1601_05362_gb300 import blcoc
@@ -299,21 +330,25 @@ def test_plain_block_methods_full_solve(method):
     assert info["relres_true"] < 1e-8
 
 
-@pytest.mark.parametrize("p", [5, 8, 13, 16])
-def test_fp64_tc_option_matches_oracle(p):
+@pytest.mark.parametrize("method,p", [("cocr_rq", p) for p in (5, 8, 13, 16, 17, 24, 32)] +
+                         [("cocg_rq", p) for p in (5, 8, 16, 21, 32)])
+def test_fp64_tc_option_matches_oracle(method, p):
     """Option fp64_tc: the p x p block updates run on the bf16 tensor cores by exact
-    integer slicing; the iterates must match the FP64 oracle like the FP64-FMA path."""
+    integer slicing; the iterates must match the FP64 oracle like the FP64-FMA path.
+    Widths 17-32 run the kernels whose slice digits are staged in shared memory (K = 64
+    real columns, level sums still exact in fp32)."""
     torch = need_gpu()
     n = 1500 + 3 * p
     A = P.random_complex_symmetric(n, 8, seed=100 + p, diag=3.0 + 0.6j, scale=0.25)
     Bh = P.complex_normal(n, p, 200 + p)
     X0 = 0.1 * P.complex_normal(n, p, 300 + p)
-    ref = O.bl_cocr_rq(A.to_scipy(), Bh, X0=X0, tol=0.0, maxit=12)
+    f = O.bl_cocr_rq if method == "cocr_rq" else O.bl_cocg_rq
+    ref = f(A.to_scipy(), Bh, X0=X0, tol=0.0, maxit=12)
     h = _handle(A)
     h.set_option("fp64_tc", 1)
     B = to_dev(torch, Bh)
     X = to_dev(torch, X0)
-    assert h.solve(B, X, tol=0.0, maxit=12) == 5
+    assert h.solve(B, X, method=method, tol=0.0, maxit=12) == 5
     hist = h.info()["hist"]
     assert np.max(np.abs(hist - np.array(ref.hist)) / np.array(ref.hist)) < HIST_TOL
     assert rel(X.cpu().numpy(), ref.X) < X_TOL
@@ -343,10 +378,11 @@ def test_fp64_tc_full_solve_helmholtz2d():
 
 
 @pytest.mark.parametrize("method", ["cocg_rq", "cocr_rq"])
-@pytest.mark.parametrize("p", [1, 4, 7, 16])
-def test_cholqr2_option_matches_oracle(method, p):
+@pytest.mark.parametrize("p,tc", [(1, 0), (4, 0), (7, 0), (16, 0), (7, 1), (16, 1), (32, 1)])
+def test_cholqr2_option_matches_oracle(method, p, tc):
     """Option qr_passes = 2 (CholQR2: a second pass W <- W T1 and a second Cholesky factor
-    after every Cholesky QR, setup included) against the oracle's Householder QR."""
+    after every Cholesky QR, setup included) against the oracle's Householder QR, also with
+    the block updates on the tensor cores (the second factor's slices feed the passes)."""
     torch = need_gpu()
     n = 1500 + 3 * p
     A = P.random_complex_symmetric(n, 8, seed=100 + p, diag=3.0 + 0.6j, scale=0.25)
@@ -357,6 +393,7 @@ def test_cholqr2_option_matches_oracle(method, p):
     ref = f(A.to_scipy(), Bh, X0=X0, tol=0.0, maxit=m)
     h = _handle(A)
     h.set_option("qr_passes", 2)
+    h.set_option("fp64_tc", tc)
     B = to_dev(torch, Bh)
     X = to_dev(torch, X0)
     assert h.solve(B, X, method=method, tol=0.0, maxit=m) == 5, h.last_error()
