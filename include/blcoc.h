@@ -120,8 +120,8 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
  * B[i], X[i]: device pointers.  ms_per_iter_out (may be NULL): device time per
  * system-iteration over the whole batch.  Per-system results: blcoc_get_info(hs[i]).
  * Returns BLCOC_OK if every system converged, else the first non-OK status.
- * Each system runs with its own handle's options (fp64_tc, u_explicit, qr_passes), as
- * blcoc_solve would.
+ * Each system runs with its own handle's options (fp64_tc, u_explicit, qr_passes,
+ * qr_fallback), as blcoc_solve would.
  * The paper solves one system at a time; batching many is this library's addition.
  */
 blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* const* B, void* const* X,
@@ -131,7 +131,8 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
 /*
  * blcoc_solve_batched_persistent - the same batch (arguments, results and statuses as
  * blcoc_solve_batched; p[i] <= 16, rq methods, handles without the options qr_passes = 2,
- * fp64_tc and u_explicit) with every iteration of every system in
+ * fp64_tc and u_explicit; the shifted-CholQR3 fallback of option qr_fallback is not run,
+ * so a failed Cholesky QR is a breakdown) with every iteration of every system in
  * ONE persistent kernel launch.  An iteration of Algorithm 2 or 3 (Sec. 2.2) is a chain
  * of stages per system (row passes, their reductions, the p x p stages); the items of a
  * stage (a row pass's 32-row chunk groups, the reduction slices, one p x p solve) wait in
@@ -142,7 +143,7 @@ blcoc_status blcoc_solve_batched(int nsys, const blcoc_handle* hs, const void* c
  * nothing more (convergence mask).  The launch and the copies that arm it are one CUDA
  * graph (a direct launch if capture is refused; blcoc_get_stat(hs[0], "persistent_graph")
  * says which).  Each system's iterates, history and residuals are bitwise those of a
- * separate blcoc_solve.
+ * separate blcoc_solve (with qr_fallback = 0 where that fallback would have run).
  * With autotune != 0, successive calls with the same batch signature (every system's n,
  * nnz and p) time the candidate grid sizes (resident CTAs per SM) in turn and then keep
  * the fastest per system-iteration; blcoc_last_error(hs[0]) names the shape used.
@@ -238,6 +239,16 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  Cholesky factor tau2 follows and tau = tau2 tau1 (error about cond(W)
  *                  eps, like a Householder QR).  One extra read/write pass of W per
  *                  iteration.  Not available in blcoc_solve_batched_persistent.
+ *   "qr_fallback": BLCOC_COCR_RQ with qr_passes = 1: 1 (default) - when the Cholesky QR of
+ *                  a residual block fails (a pivot not above 64 eps of its column's
+ *                  squared norm: the block is too ill-conditioned for cond^2 eps), it is
+ *                  redone as shifted CholQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+ *                  Yanagisawa): Cholesky of W^H W + s I with s = 11 (n p + p(p+1)) u
+ *                  trace(W^H W), then two Cholesky QR passes; a breakdown is reported
+ *                  only if the resulting factor has a diagonal entry below 1e-14 of its
+ *                  largest (the rank test of a Householder QR).  The six kernels of the
+ *                  fallback are in every iteration and return at once unless it is
+ *                  needed.  0: a failed Cholesky QR is a breakdown.
  *   "spmm_split" : the SpMM's row bundle.  1 (default): p lanes per row (one per column),
  *                  each summing the row's nonzeros in order.  2 or 4: that many lane groups
  *                  split each row's nonzeros (interleaved) and their partial sums are

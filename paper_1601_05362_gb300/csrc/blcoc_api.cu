@@ -91,9 +91,10 @@ struct GraphKey {
   int tc = 0;        // tensor-core block updates
   int qr2 = 0;       // CholQR2
   int split = 0;     // SpMM row bundle
+  int qr_fb = 0;     // shifted-CholQR3 fallback passes present
   bool operator==(const GraphKey& o) const {
     return method == o.method && mixed == o.mixed && uexpl == o.uexpl && plain == o.plain && tc == o.tc &&
-           qr2 == o.qr2 && split == o.split;
+           qr2 == o.qr2 && split == o.split && qr_fb == o.qr_fb;
   }
 };
 
@@ -160,6 +161,7 @@ struct blcoc_ctx {
   int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
   int u_explicit_mixed = 1;   // the same for the complex64 inner solves
   int qr_passes = 1;          // 2: CholQR2 (one re-orthogonalising pass after every Cholesky QR)
+  int qr_fallback = 1;        // cocr, qr_passes = 1: shifted-CholQR3 fallback when a Cholesky QR fails
   int spmm_split = 1;         // SpMM row bundle (1, 2, 4); 0: timed sweep, cached per (n, nnz/row, p)
   int stat_spmm_split = 0;    // row bundle of the last solve
   int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
@@ -364,10 +366,10 @@ struct Solver {
     time_small = mode == 1;
     time_only = mode == 3 ? (method == BLCOC_COCR_RQ ? (int)K_COCR_C : (int)K_COCG_1) : -1;
   }
-  void reduce(int ne, const Ctrl* ctrl) {
+  void reduce(int ne, const Ctrl* ctrl, bool fb_only = false) {
     Timer t;
     if (time_small) timed_begin(t, kKindReduce);
-    launch_reduce(h->partials, last_grid, ne, h->stage1, ctrl, h->s);
+    launch_reduce(h->partials, last_grid, ne, h->stage1, ctrl, h->s, fb_only);
     if (time_small) timed_end(t);
     ++launches;
   }
@@ -399,6 +401,19 @@ struct Solver {
     reduce(E, h->ctrl);
     small(setup ? SK_CHOL2_SETUP : SK_CHOL2, E);
   }
+  // Shifted-CholQR3 fallback (bl_cocr_rq with single-pass Cholesky QR): when the p x p
+  // stage before had to shift the Gram, two Cholesky QR passes complete the factorisation;
+  // otherwise these kernels return at once.
+  int qr_fb = 0;
+  void fallback_qr(bool setup) {
+    if (!qr_fb) return;
+    const int E = tri_count(p);
+    for (int k = 0; k < 2; ++k) {
+      pass(K->qr2, K_QR2, E, F_FB, nullptr, kKindQR2);
+      reduce(E, h->ctrl, true);
+      small(setup ? SK_CHOL_FB_SETUP : SK_CHOL_FB, E);
+    }
+  }
 
   // inner = 1: the right-hand side of this solve is the residual itself (refinement
   // step), so the stopping test is relative to ||R||_F instead of ||B||_F.
@@ -408,6 +423,7 @@ struct Solver {
     reduce(2 * E + 1, h->ctrl);
     small(inner ? SK_SETUP_INNER : SK_SETUP, 2 * E + 1);
     second_qr(true);
+    fallback_qr(true);
   }
   void setup_rest() {
     const int E = tri_count(p);
@@ -432,6 +448,7 @@ struct Solver {
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
       second_qr(false);
+      fallback_qr(false);
       pass(spmm_fn(), K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (for H+ of the beta' step)
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
@@ -458,6 +475,7 @@ struct Solver {
       reduce(E, h->ctrl);
       small(SK_CHOL, E);
       second_qr(false);
+      fallback_qr(false);
       pass(spmm_fn(), K_SPMM_GRAM, E, 1);
       reduce(E, h->ctrl);
       small(SK_COCR_BETA, E);
@@ -488,6 +506,14 @@ struct Solver {
     ++launches;
   }
 };
+
+// Control-block fields of the shifted-CholQR3 fallback: on, and the shift coefficient
+// 11 (n p + p (p + 1)) u of Fukaya et al. (applied to trace(W^H W) >= ||W||_2^2).
+void set_qr_fallback(Ctrl& c, int on, int64_t n, int p) {
+  c.qr_fb_on = on;
+  c.qr_fb = 0;
+  c.qr_shift = on ? 11.0 * ((double)n * p + (double)p * (p + 1)) * 0x1p-53 : 0.0;
+}
 
 bool is_host_ptr(const void* ptr) {
   cudaPointerAttributes at{};
@@ -703,6 +729,12 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
     if (value != 0 && value != 1 && value != 2 && value != 4) return invalid(h, "spmm_split must be 0, 1, 2 or 4");
     h->graph.reset();
     h->spmm_split = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "qr_fallback")) {
+    if (value != 0 && value != 1) return invalid(h, "qr_fallback must be 0 or 1");
+    h->graph.reset();
+    h->qr_fallback = (int)value;
     return BLCOC_OK;
   }
   if (!strcmp(key, "qr_passes")) {
@@ -1315,11 +1347,13 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   sv.plain = plain ? 1 : 0;
   sv.uexpl = !plain && h->u_explicit != 0;
   sv.qr2 = h->qr_passes == 2 ? 1 : 0;
+  sv.qr_fb = (!plain && base_method == BLCOC_COCR_RQ && !sv.qr2 && h->qr_fallback) ? 1 : 0;
   sv.spmm_split = h->spmm_split == 0 ? tune_spmm_split(h, sv, tc) : h->spmm_split;
   h->stat_spmm_split = sv.spmm_fn() == sv.K->spmm_gram ? 1 : sv.spmm_split;
   Ctrl c0{};
   c0.maxit = maxit;
   c0.tol = tol;
+  set_qr_fallback(c0, sv.qr_fb, h->n, p);
   CK(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->s));
   {
     NvtxRange r("blcoc setup");
@@ -1342,6 +1376,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
     gkey.plain = sv.plain;
     gkey.tc = tc ? 1 : 0;
     gkey.qr2 = sv.qr2;
+    gkey.qr_fb = sv.qr_fb;
     gkey.split = h->stat_spmm_split;
     st = run_iterations(h, sv, gkey, maxit);
     if (st != BLCOC_OK) return st;
@@ -1435,6 +1470,9 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     sv.back().use_fp64_blocks();
     sv.back().qr2 = h->qr_passes == 2 ? 1 : 0;
     sv.back().uexpl = method == BLCOC_COCR_RQ && h->u_explicit != 0;
+    // the graph form runs the shifted-CholQR3 fallback as blcoc_solve does; the persistent
+    // kernel has no stages for it
+    sv.back().qr_fb = (form == 0 && method == BLCOC_COCR_RQ && !sv.back().qr2 && h->qr_fallback) ? 1 : 0;
     if (form == 0) {   // SpMM row bundle: the handle's, or timed per (n, nnz/row, p) when autotuning
       const bool tc_i = sv.back().oz != nullptr;
       sv.back().spmm_split = (autotune || h->spmm_split == 0) ? tune_spmm_split(h, sv.back(), tc_i) : h->spmm_split;
@@ -1443,6 +1481,7 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     Ctrl c0{};
     c0.maxit = maxit;
     c0.tol = tol;
+    set_qr_fallback(c0, sv.back().qr_fb, h->n, p[i]);
     CK(h, cudaMemcpyAsync(h->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, h->s));
     sv.back().setup_residual();
     CK(h, cudaMemcpyAsync(h->h_ctrl, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->s));

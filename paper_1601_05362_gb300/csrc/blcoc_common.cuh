@@ -33,13 +33,20 @@ struct Ctrl {
   int bd_code;    // breakdown site: 1 setup QR, 2 alpha solve, 3 QR, 4 beta solve, 5 non-finite xi
   int nhist;      // entries of the residual history written so far
   int hlu_ok;     // cocr: the LU factors of H_m in slots M_HLU (beside the alpha' step) are valid
+  int qr_fb;      // shifted-CholQR3 fallback: re-orthogonalising passes still to run (0: none)
+  int qr_fb_on;   // the fallback is enabled for this solve (bl_cocr_rq, single-pass Cholesky QR)
   double tol;
   double nb;      // ||B||_F
   double relres;  // ||xi_iter||_F / ||B||_F
   double trr;     // ||B - A X||_F (after the final residual pass)
   double sumsq_b; // sum |B_ij|^2 (setup)
   double pad[2];
+  double qr_shift; // fallback shift coefficient 11 (n p + p (p + 1)) u (times trace(W^H W))
 };
+
+// PassArgs::flag bit shared with the host: the row pass runs only while a shifted-CholQR3
+// fallback is in progress (Ctrl::qr_fb > 0); the other bits are in blcoc_rowpass.cuh.
+constexpr int F_FB = 32;
 
 // p x p complex matrices live in one device array of slots, each PMAX*PMAX entries,
 // row-major with row stride p (dense p x p in the first p*p entries).

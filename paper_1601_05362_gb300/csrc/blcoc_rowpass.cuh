@@ -664,6 +664,7 @@ constexpr int F_FORCE = 16;     // run even when the control block says the solv
 
 #define BLCOC_PROLOGUE(CT)                                          \
   if (!(a.flag & F_FORCE) && BLCOC_LD(&a.ctrl->done)) return;       \
+  if ((a.flag & F_FB) && BLCOC_LD(&a.ctrl->qr_fb) == 0) return;     \
   extern __shared__ __align__(16) unsigned char smem_raw[];         \
   CT* smem = reinterpret_cast<CT*>(smem_raw);                       \
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;       \

@@ -10,8 +10,9 @@ namespace blcoc {
 // CTA sums q = q0 + g, q0 + g + 4, ... in turn, and the four warp sums are combined as
 // (a0 + a1) + (a2 + a3).  Each thread thus issues about nparts / 64 independent loads.
 __global__ void __launch_bounds__(128) k_reduce_stage1(const double* __restrict__ partials, int nparts, int ncomp,
-                                                       double* __restrict__ stage1, const Ctrl* ctrl) {
+                                                       double* __restrict__ stage1, const Ctrl* ctrl, int fb_only) {
   if (ctrl != nullptr && ctrl->done) return;
+  if (fb_only && ctrl != nullptr && ctrl->qr_fb == 0) return;
   __shared__ double part[4][32];
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
@@ -61,6 +62,12 @@ __global__ void k_small_chol2(int p, int method, const double* stage1, int ncomp
 }
 
 // One CTA per group of columns of beta' (gridDim.x groups).
+__global__ void k_small_chol_fb(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
+                                int setup, uint2* oz) {
+  SMALL_PROLOGUE
+  d_small_chol_fb(S, p, method, stage1, ncomp, mats, ctrl, setup, oz);
+}
+
 __global__ void k_small_cocr_beta(int p, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl, uint2* oz) {
   SMALL_PROLOGUE
   const int per = (p + gridDim.x - 1) / gridDim.x;
@@ -137,6 +144,7 @@ static void set_small_attrs() {
   cudaFuncSetAttribute(k_small_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_chol2, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_chol_fb, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_cocr_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_trr, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   done[dev] = true;
@@ -144,10 +152,12 @@ static void set_small_attrs() {
 
 void prepare_small_kernels() { set_small_attrs(); }
 
-void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s) {
+void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s,
+                   bool fb_only) {
   const int ncomp = 2 * ne;
   dim3 grid((ncomp + 31) / 32, RED_SPLIT);
-  k_reduce_stage1<<<grid, 128, 0, s>>>(reinterpret_cast<const double*>(partials), nparts, ncomp, stage1, ctrl);
+  k_reduce_stage1<<<grid, 128, 0, s>>>(reinterpret_cast<const double*>(partials), nparts, ncomp, stage1, ctrl,
+                                       fb_only ? 1 : 0);
 }
 
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
@@ -165,6 +175,8 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
       break;
     case SK_CHOL2: k_small_chol2<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, oz); break;
     case SK_CHOL2_SETUP: k_small_chol2<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, oz); break;
+    case SK_CHOL_FB: k_small_chol_fb<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 0, oz); break;
+    case SK_CHOL_FB_SETUP: k_small_chol_fb<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, 1, oz); break;
     case SK_COCR_H0: k_small_cocr_H0<<<1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl); break;
     case SK_ALPHA:
       k_small_alpha<<<m == 1 ? 2 : 1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz);

@@ -4,11 +4,14 @@
 
 namespace blcoc {
 
-enum SmallKind { SK_SETUP = 0, SK_COCR_H0, SK_ALPHA, SK_CHOL, SK_COCR_BETA, SK_TRR, SK_SETUP_INNER, SK_CHOL2, SK_CHOL2_SETUP };
+enum SmallKind { SK_SETUP = 0, SK_COCR_H0, SK_ALPHA, SK_CHOL, SK_COCR_BETA, SK_TRR, SK_SETUP_INNER, SK_CHOL2, SK_CHOL2_SETUP,
+                 SK_CHOL_FB, SK_CHOL_FB_SETUP };
 
 void prepare_small_kernels();
 // ctrl == nullptr: run even after the solve has finished (final residual pass).
-void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s);
+// fb_only: run only while a shifted-CholQR3 fallback is in progress (ctrl->qr_fb > 0).
+void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, const Ctrl* ctrl, cudaStream_t s,
+                   bool fb_only = false);
 // method: 0 cocg / 1 cocr, + 16 for the plain forms, + 32 for CholQR2.
 // oz != nullptr: also write the exact-slice fragments of the factors formed (tensor-core
 // applies of the FP64 path, p <= 16).

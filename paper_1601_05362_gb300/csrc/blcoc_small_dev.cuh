@@ -402,6 +402,33 @@ __device__ void gstore_cols(double2* mats, int sl, const double2* s, int p, int 
   __syncthreads();
 }
 
+// Cholesky factor of the Hermitian Gram in S.gs (its triangle): tau^H tau = G, tau in
+// S.m[1].  With the fallback on (ctrl->qr_fb_on), a factorisation that fails the pivot test
+// is retried on G + s I with s = ctrl->qr_shift * trace(G) >= 11 (n p + p(p+1)) u ||W||_2^2,
+// the shift of shifted CholQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa), which
+// makes the factorisation succeed for any W of condition below about u^-1; the two
+// Cholesky QR passes that complete it then run (ctrl->qr_fb = 2, stage d_small_chol_fb).
+__device__ bool chol_gram(SmallShared& S, int p, Ctrl* ctrl) {
+  expand_tri(S.gs, S.m[0], p, true);
+  if (chol_upper(S.m[0], S.m[1], p, S.red)) return true;
+  if (!BLCOC_LD(&ctrl->qr_fb_on) || !(ctrl->qr_shift > 0.0)) return false;
+  expand_tri(S.gs, S.m[0], p, true);
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int j = 0; j < p; ++j) tr += S.m[0][j * LD + j].x;
+    S.red[0] = ctrl->qr_shift * tr;
+  }
+  __syncthreads();
+  const double sh = S.red[0];
+  __syncthreads();
+  for (int j = threadIdx.x; j < p; j += blockDim.x) S.m[0][j * LD + j].x += sh;
+  __syncthreads();
+  if (!chol_upper(S.m[0], S.m[1], p, S.red)) return false;
+  if (threadIdx.x == 0) ctrl->qr_fb = 2;
+  __syncthreads();
+  return true;
+}
+
 // Setup after the residual pass: ||B||_F, Q_0 xi_0 = R_0 (Cholesky QR), T_0 = xi_0^{-1};
 // cocg: G_QQ = Q_0^T Q_0 = T^T (R^T R) T.
 // inner = 1 (refinement step): the stopping test is relative to ||R_0||_F, the norm of
@@ -443,8 +470,7 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
     }
     return;
   }
-  expand_tri(S.gs, S.m[0], p, true);
-  if (!chol_upper(S.m[0], S.m[1], p, S.red)) {
+  if (!chol_gram(S, p, ctrl)) {
     if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 1; }
     return;
   }
@@ -549,8 +575,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
     __syncthreads();
     return;
   }
-  expand_tri(S.gs, S.m[0], p, true);
-  if (!chol_upper(S.m[0], S.m[1], p, S.red)) {
+  if (!chol_gram(S, p, ctrl)) {
     if (threadIdx.x == 0) {
       ctrl->done = 3;
       ctrl->bd_code = 3;
@@ -637,6 +662,36 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
   }
   gstore_fac(mats, M_TINV, S.m[2], p);
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
+}
+
+// Shifted-CholQR3 fallback, one of its two Cholesky QR passes (after the row pass
+// W <- W T_prev with Gram W^H W): the CholQR2 second-factor step (tau <- tau_k tau, xi
+// updated, T_k stored for the passes that follow).  Runs only while ctrl->qr_fb > 0.  After
+// the last pass the whole factor tau must keep its rank the way the oracle's Householder
+// QR is judged: a diagonal entry below 1e-14 of the largest is a breakdown.
+__device__ __noinline__ void d_small_chol_fb(SmallShared& S, int p, int method, const double* stage1, int ncomp,
+                                             double2* mats, Ctrl* ctrl, int setup, uint2* oz) {
+  if (BLCOC_LD(&ctrl->done) || BLCOC_LD(&ctrl->qr_fb) == 0) return;
+  d_small_chol2(S, p, method, stage1, ncomp, mats, ctrl, setup, oz);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int left = ctrl->qr_fb - 1;
+    ctrl->qr_fb = left;
+    if (left == 0 && !ctrl->done) {
+      const double2* tau = slot(mats, setup ? M_XI : M_TAU);
+      double dmax = 0.0, dmin = 1e308;
+      for (int j = 0; j < p; ++j) {
+        const double d = fabs(tau[j * p + j].x);
+        dmax = fmax(dmax, d);
+        dmin = fmin(dmin, d);
+      }
+      if (!(dmin > 1e-14 * dmax)) {
+        ctrl->done = 3;
+        ctrl->bd_code = setup ? 1 : 3;
+        if (!setup && method == 1) ctrl->iter -= 1;
+      }
+    }
+  }
 }
 
 // cocr, beside the alpha' step (Algorithm 3): the elimination of H_m = Q_m^T V_m (slot M_H,

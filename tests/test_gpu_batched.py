@@ -152,3 +152,35 @@ def test_batch_of_config_sized_systems_matches_oracle(persistent):
         assert np.max(np.abs(info["hist"] - np.array(ref.hist)) / np.array(ref.hist)) < 1e-8, pr.name
         assert rel(X.cpu().numpy(), ref.X) < 1e-10, pr.name
         h.close()
+
+
+def test_batched_graph_runs_the_qr_fallback_like_separate_solves():
+    """Tiny systems near finite termination lose rank to the single-pass Cholesky QR's
+    resolution (one of these 40 does at iteration 6); blcoc_solve then completes the QR as
+    shifted CholQR3 and converges.  The graph form runs the same fallback per handle, so
+    every system equals its separate solve bit for bit, with the same status."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    tiny = P.helmholtz2d_batch(40, seed=11, side_range=(6, 14), k_range=(2.0, 5.0))
+
+    def run(batched):
+        hs = [blcoc.Handle.from_csr(pr.A) for pr in tiny]
+        Bs = [to_dev(torch, pr.B) for pr in tiny]
+        Xs = [torch.zeros_like(B) for B in Bs]
+        if batched:
+            st, _, _ = blcoc.solve_batched(hs, Bs, Xs, tol=1e-10, maxit=30, autotune=False)
+            sts = None
+        else:
+            sts = [h.solve(B, X, tol=1e-10, maxit=30) for h, B, X in zip(hs, Bs, Xs)]
+            st = max(sts)
+        out = [(X.cpu().numpy(), h.info()) for X, h in zip(Xs, hs)]
+        for h in hs:
+            h.close()
+        return st, sts, out
+
+    st_g, _, graph = run(True)
+    st_s, sts, sep = run(False)
+    assert st_g == st_s
+    for (Xg, ig), (Xs_, is_) in zip(graph, sep):
+        assert ig["iters"] == is_["iters"]
+        assert np.array_equal(Xg, Xs_) and np.array_equal(ig["hist"], is_["hist"])

@@ -228,6 +228,38 @@ def test_breakdown_on_nearly_dependent_columns_agrees_with_oracle(method, gap, e
     h.close()
 
 
+def test_shifted_cholqr3_fallback_on_ill_conditioned_right_hand_sides():
+    """Columns dependent to 1e-10: a Cholesky QR cannot resolve them (cond^2 eps >> 1), a
+    Householder QR can.  The oracle (Householder) converges.  bl_cocr_rq with the shifted
+    CholQR3 fallback (default) converges to the tolerance as well and its QR factor xi_0
+    matches the oracle's where it is resolved; without the fallback, and for bl_cocg_rq
+    (which has none), the solve reports a breakdown at the setup QR."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    A = P.random_complex_symmetric(600, 8, seed=41, diag=3.0 + 0.6j, scale=0.25)
+    Bh = P.complex_normal(A.n, 4, 42)
+    Bh[:, 3] = Bh[:, 0] * (1.0 + 1e-10 * P.complex_normal(A.n, 1, 43)[:, 0])
+    for f in (O.bl_cocr_rq, O.bl_cocg_rq):
+        assert f(A.to_scipy(), Bh, tol=1e-10, maxit=500).status == O.CONVERGED
+    ref0 = O.bl_cocr_rq(A.to_scipy(), Bh, tol=0.0, maxit=0)
+    B = to_dev(torch, Bh)
+    h = _handle(A)
+    X = torch.zeros_like(B)
+    assert h.solve(B, X, method="cocr_rq", tol=0.0, maxit=0) == blcoc.BLCOC_NOT_CONVERGED, h.last_error()
+    d_gpu, d_ref = np.abs(np.diag(h.xi(4))), np.abs(np.diag(ref0.xi))
+    assert np.max(np.abs(d_gpu - d_ref) / d_ref) < 1e-4, (d_gpu, d_ref)
+    X.zero_()
+    assert h.solve(B, X, method="cocr_rq", tol=1e-10, maxit=500) == blcoc.BLCOC_OK, h.last_error()
+    assert O.true_relres(A.to_scipy(), Bh, X.cpu().numpy()) <= 1e-9
+    h.set_option("qr_fallback", 0)
+    X.zero_()
+    assert h.solve(B, X, method="cocr_rq", tol=1e-10, maxit=500) == blcoc.BLCOC_BREAKDOWN
+    h.set_option("qr_fallback", 1)
+    X.zero_()
+    assert h.solve(B, X, method="cocg_rq", tol=1e-10, maxit=500) == blcoc.BLCOC_BREAKDOWN
+    h.close()
+
+
 def test_create_rejects_bad_matrices():
     need_gpu()
     from paper_1601_05362_gb300 import blcoc
