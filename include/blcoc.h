@@ -239,7 +239,7 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  Cholesky factor tau2 follows and tau = tau2 tau1 (error about cond(W)
  *                  eps, like a Householder QR).  One extra read/write pass of W per
  *                  iteration.  Not available in blcoc_solve_batched_persistent.
- *   "qr_fallback": BLCOC_COCR_RQ with qr_passes = 1: 1 (default) - when the Cholesky QR of
+ *   "qr_fallback": rq methods with qr_passes = 1: 1 (default) - when the Cholesky QR of
  *                  a residual block fails (a pivot not above 64 eps of its column's
  *                  squared norm: the block is too ill-conditioned for cond^2 eps), it is
  *                  redone as shifted CholQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto,

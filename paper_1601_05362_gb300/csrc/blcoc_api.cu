@@ -161,7 +161,7 @@ struct blcoc_ctx {
   int u_explicit = 0;         // cocr: U_{m+1} = A S_{m+1} by SpMM instead of V + U beta'
   int u_explicit_mixed = 1;   // the same for the complex64 inner solves
   int qr_passes = 1;          // 2: CholQR2 (one re-orthogonalising pass after every Cholesky QR)
-  int qr_fallback = 1;        // cocr, qr_passes = 1: shifted-CholQR3 fallback when a Cholesky QR fails
+  int qr_fallback = 1;        // rq methods, qr_passes = 1: shifted-CholQR3 fallback when a Cholesky QR fails
   int spmm_split = 1;         // SpMM row bundle (1, 2, 4); 0: timed sweep, cached per (n, nnz/row, p)
   int stat_spmm_split = 0;    // row bundle of the last solve
   int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
@@ -394,24 +394,25 @@ struct Solver {
     return K->spmm_gram;
   }
   // CholQR2's second pass and factor (setup: the factor of R_0)
+  // (cocg: the pass also forms Q1^T Q1, from which the stage forms Q^T Q of the final basis)
   void second_qr(bool setup) {
     if (!qr2 || plain) return;
-    const int E = tri_count(p);
-    pass(K->qr2, K_QR2, E, 0, nullptr, kKindQR2);
-    reduce(E, h->ctrl);
-    small(setup ? SK_CHOL2_SETUP : SK_CHOL2, E);
+    const int E = tri_count(p), ne = method == BLCOC_COCG_RQ ? 2 * E : E;
+    pass(K->qr2, K_QR2, ne, method == BLCOC_COCG_RQ ? F_SYM2 : 0, nullptr, kKindQR2);
+    reduce(ne, h->ctrl);
+    small(setup ? SK_CHOL2_SETUP : SK_CHOL2, ne);
   }
-  // Shifted-CholQR3 fallback (bl_cocr_rq with single-pass Cholesky QR): when the p x p
+  // Shifted-CholQR3 fallback (rq methods with single-pass Cholesky QR): when the p x p
   // stage before had to shift the Gram, two Cholesky QR passes complete the factorisation;
   // otherwise these kernels return at once.
   int qr_fb = 0;
   void fallback_qr(bool setup) {
     if (!qr_fb) return;
-    const int E = tri_count(p);
+    const int E = tri_count(p), ne = method == BLCOC_COCG_RQ ? 2 * E : E;
     for (int k = 0; k < 2; ++k) {
-      pass(K->qr2, K_QR2, E, F_FB, nullptr, kKindQR2);
-      reduce(E, h->ctrl, true);
-      small(setup ? SK_CHOL_FB_SETUP : SK_CHOL_FB, E);
+      pass(K->qr2, K_QR2, ne, F_FB | (method == BLCOC_COCG_RQ ? F_SYM2 : 0), nullptr, kKindQR2);
+      reduce(ne, h->ctrl, true);
+      small(setup ? SK_CHOL_FB_SETUP : SK_CHOL_FB, ne);
     }
   }
 
@@ -487,6 +488,7 @@ struct Solver {
       reduce(2 * E, h->ctrl);
       small(SK_CHOL, 2 * E);
       second_qr(false);
+      fallback_qr(false);
       pass(K->cocg_pass2, K_COCG_2, 0, 0);
       pass(spmm_fn(), K_SPMM_GRAM, E, 0, base().S);   // A S_{m+1}, gram S^T A S
       reduce(E, h->ctrl);
@@ -1347,7 +1349,7 @@ blcoc_status blcoc_solve(blcoc_handle h, const void* B, void* X, int p, blcoc_me
   sv.plain = plain ? 1 : 0;
   sv.uexpl = !plain && h->u_explicit != 0;
   sv.qr2 = h->qr_passes == 2 ? 1 : 0;
-  sv.qr_fb = (!plain && base_method == BLCOC_COCR_RQ && !sv.qr2 && h->qr_fallback) ? 1 : 0;
+  sv.qr_fb = (!plain && !sv.qr2 && h->qr_fallback) ? 1 : 0;
   sv.spmm_split = h->spmm_split == 0 ? tune_spmm_split(h, sv, tc) : h->spmm_split;
   h->stat_spmm_split = sv.spmm_fn() == sv.K->spmm_gram ? 1 : sv.spmm_split;
   Ctrl c0{};
@@ -1472,7 +1474,7 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     sv.back().uexpl = method == BLCOC_COCR_RQ && h->u_explicit != 0;
     // the graph form runs the shifted-CholQR3 fallback as blcoc_solve does; the persistent
     // kernel has no stages for it
-    sv.back().qr_fb = (form == 0 && method == BLCOC_COCR_RQ && !sv.back().qr2 && h->qr_fallback) ? 1 : 0;
+    sv.back().qr_fb = (form == 0 && !sv.back().qr2 && h->qr_fallback) ? 1 : 0;
     if (form == 0) {   // SpMM row bundle: the handle's, or timed per (n, nnz/row, p) when autotuning
       const bool tc_i = sv.back().oz != nullptr;
       sv.back().spmm_split = (autotune || h->spmm_split == 0) ? tune_spmm_split(h, sv.back(), tc_i) : h->spmm_split;

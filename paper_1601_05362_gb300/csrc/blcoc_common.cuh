@@ -34,7 +34,7 @@ struct Ctrl {
   int nhist;      // entries of the residual history written so far
   int hlu_ok;     // cocr: the LU factors of H_m in slots M_HLU (beside the alpha' step) are valid
   int qr_fb;      // shifted-CholQR3 fallback: re-orthogonalising passes still to run (0: none)
-  int qr_fb_on;   // the fallback is enabled for this solve (bl_cocr_rq, single-pass Cholesky QR)
+  int qr_fb_on;   // the fallback is enabled for this solve (rq methods, single-pass Cholesky QR)
   double tol;
   double nb;      // ||B||_F
   double relres;  // ||xi_iter||_F / ||B||_F
@@ -47,6 +47,8 @@ struct Ctrl {
 // PassArgs::flag bit shared with the host: the row pass runs only while a shifted-CholQR3
 // fallback is in progress (Ctrl::qr_fb > 0); the other bits are in blcoc_rowpass.cuh.
 constexpr int F_FB = 32;
+// PassArgs::flag bit: the residual pass also forms R^T R, the CholQR2 pass also Q1^T Q1.
+constexpr int F_SYM2 = 2;
 
 // p x p complex matrices live in one device array of slots, each PMAX*PMAX entries,
 // row-major with row stride p (dense p x p in the first p*p entries).
@@ -58,7 +60,7 @@ enum MatSlot {
   M_ALPHAXI,     // alpha'_m xi_m
   M_BETA,        // beta'_m
   M_H,           // cocr: H_m = Q_m^T V_m;  cocg: G_QQ = Q_m^T Q_m
-  M_G1,          // CholQR2 with cocg: W^T W (R^T R at setup) kept for the second factor
+  M_G1,          // spare
   // Three-product forms of the factors the FP64 row passes apply (T, alpha', alpha'xi,
   // beta'): entry (k, j) of M = Mr + i Mi is kept as Mr and (Mr + Mi, Mi - Mr), so that a
   // complex product y M costs three real products (Gauss): with s = y.re + y.im,

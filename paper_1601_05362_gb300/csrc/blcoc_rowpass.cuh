@@ -250,6 +250,13 @@ __device__ __forceinline__ void apply_full(typename Cx<S>::T* out, const typenam
 // relative to |y| |M| (the terms are bounded by (|a| + |b|)(|c| + |d|) <= 2 |y| |M|).
 template <int PP, typename S, bool OZ = false>
 constexpr bool m3_apply() { return sizeof(S) == 8 && !OZ && PP >= 8; }
+// FP64 passes at p = 32 keep one tile per warp: the second operand of each block update
+// (and W in the SpMM's Gram) is read from global memory through L1 (lane = row; a 128-byte
+// line serves 8 consecutive columns of a row) instead of a second 16 KB tile, so that two
+// 4-warp CTAs fit an SM instead of one (two warps per SM sub-partition instead of one).
+template <int PP, typename S, bool OZ>
+constexpr bool one_tile() { return PP >= 32 && sizeof(S) == 8 && !OZ; }
+
 // Tensor-core Grams (exact slices, per-warp FP64 sums in shared memory) are built for
 // p <= 16; at p = 32 the tensor-core passes keep their Grams on the FP64 pipe (the sums
 // of 64 x 64 real entries per warp would not fit beside the tiles).
@@ -270,6 +277,10 @@ __device__ __forceinline__ void oz_apply_any(double2* out, const double2* base, 
 }
 template <int PP, typename S>
 constexpr bool m3_gram() { return sizeof(S) == 8 && PP >= 8; }
+// The CholQR2 pass (which also forms Q1^T Q1 for bl_cocg_rq): three-product Grams from a
+// companion tile up to p = 16; at p = 32 two such accumulators would not fit in registers.
+template <int PP, typename S>
+constexpr bool qr2_m3() { return m3_gram<PP, S>() && PP <= 16; }
 
 // Three-product form of a factor, read from its slots (row stride p) through the L1 path;
 // every lane of a warp reads the same entry.
@@ -314,6 +325,36 @@ __device__ __forceinline__ void apply_full3(double2* out, const double2* base, c
     }
     for (int k = 0; k < p; ++k) {
       const double2 y = in[tix(k, lane)];
+      const double ys = y.x + y.y;
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) mac3<SUB>(acc[jj], kk[jj], y, ys, M.re(k, j0 + jj), M.sdif(k, j0 + jj));
+    }
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj)
+      if (j0 + jj < p) out[tix(j0 + jj, lane)] = make_double2(acc[jj].x + kk[jj], acc[jj].y + kk[jj]);
+  }
+}
+
+// out <- base + in * M (SUB: base - in * M), three products per MAC, with `in` read from
+// global memory: in_g = the chunk's first row of a row-major n x p block, rows = the chunk's
+// rows inside n (rows past it read as zero).  `out` may be `base`.
+template <int PP, bool SUB>
+__device__ __forceinline__ void apply_full3_g(double2* out, const double2* base, const double2* __restrict__ in_g,
+                                              int rows, const Fac3& M, int p, int lane) {
+  constexpr int JB = Geo<PP>::JB;
+  const double2* row = in_g + (int64_t)lane * p;
+  const bool live = lane < rows;
+  for (int j0 = 0; j0 < p; j0 += JB) {
+    double2 acc[JB];
+    double kk[JB];
+#pragma unroll
+    for (int jj = 0; jj < JB; ++jj) {
+      acc[jj] = (j0 + jj < p) ? base[tix(j0 + jj, lane)] : cz();
+      kk[jj] = 0.0;
+    }
+#pragma unroll 4
+    for (int k = 0; k < p; ++k) {
+      const double2 y = live ? __ldg(row + k) : cz();
       const double ys = y.x + y.y;
 #pragma unroll
       for (int jj = 0; jj < JB; ++jj) mac3<SUB>(acc[jj], kk[jj], y, ys, M.re(k, j0 + jj), M.sdif(k, j0 + jj));
@@ -470,6 +511,41 @@ struct GramAcc {
 #pragma unroll
           for (int i = 0; i < NS; ++i)
             if (i == F) mac<CONJ>(dst[i], i, Y, Z, r);
+        }
+      }
+    }
+  }
+  // FP64, Y read from global memory (Yg = the chunk's first row, rows inside n), Z a tile.
+  template <bool CONJ>
+  __device__ __forceinline__ void mac_g(double2& dst, int i, const double2* __restrict__ Yg, int rows, int p,
+                                        const double2* Z, int r) const {
+    const double2 y = r < rows ? __ldg(Yg + (int64_t)r * p + a[i]) : cz();
+    const double2 z = Z[tix(b[i], r)];
+    if constexpr (CONJ) cmac_conj(dst, y, z);
+    else cmac(dst, y, z);
+  }
+  template <bool CONJ>
+  __device__ __forceinline__ void add_g(const double2* __restrict__ Yg, int rows, int p, const double2* Z, int lane) {
+    static_assert(sizeof(S) == 8 && !M3, "FP64 four-product Gram");
+#pragma unroll 2
+    for (int r = 0; r < CHUNK; ++r) {
+#pragma unroll
+      for (int i = 0; i < NS; ++i)
+        if (i < F) mac_g<CONJ>(acc[i], i, Yg, rows, p, Z, r);
+    }
+    if (F < NS && Er > 0) {
+      if (G > 1) {
+        const int rr = CHUNK / G, r0 = (lane / Er) * rr;
+        for (int r = r0; r < r0 + rr; ++r) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i)
+            if (i == F) mac_g<CONJ>(acc[i], i, Yg, rows, p, Z, r);
+        }
+      } else if (lane < Er) {
+        for (int r = 0; r < CHUNK; ++r) {
+#pragma unroll
+          for (int i = 0; i < NS; ++i)
+            if (i == F) mac_g<CONJ>(acc[i], i, Yg, rows, p, Z, r);
         }
       }
     }
@@ -658,7 +734,7 @@ __device__ __forceinline__ double warp_sum_fixed(double v) {
 // ---------------------------------------------------------------------------------- kernels
 // PassArgs::flag bits
 constexpr int F_FIRST = 1;      // setup variant of a pass / norm-only residual / apply T
-constexpr int F_SYM2 = 2;       // residual pass: also R^T R
+// F_SYM2 (blcoc_common.cuh): residual pass also R^T R; CholQR2 pass also Q1^T Q1
 constexpr int F_UEXPL = 4;      // explicit-U variant: SpMM gram Y^T Y; pass C without the U update
 constexpr int F_FORCE = 16;     // run even when the control block says the solve is done
 
@@ -739,9 +815,10 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
+  constexpr bool OT = one_tile<PP, S, OZ>();   // W for the Gram read from global memory
   C* T_s = smem;
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
-  C* tY = tiles + warp * 2 * G::TILE;
+  C* tY = tiles + warp * (OT ? 1 : 2) * G::TILE;
   C* tW = tY + G::TILE;
   const bool applyT = a.flag & 1;
   if constexpr (G::MATS_SMEM && !M3A) {
@@ -761,11 +838,14 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     gather_rows<PP, C, false, SPL>(tY, a.A, vals_of<S>(a.A), blk<C>(a.W), nullptr, r0, p, lane, dummy0, dummy1);
-    load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
+    if (!OT && !(a.flag & F_UEXPL)) load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);   // Y^T Y needs no W
     __syncwarp();
     if constexpr (OZG) {
       if (a.flag & F_UEXPL) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tY, tY, p, lane);
       else oz_gram_add<PP, false>(zsums + warp * OzGramGeo<PP>::ACC, tW, tY, p, lane);
+    } else if constexpr (OT) {
+      if (a.flag & F_UEXPL) g.template add<false>(tY, tY, lane);
+      else g.template add_g<false>(a.W + r0 * p, (int)min((int64_t)CHUNK, n - r0), p, tY, lane);
     } else {
       g.template add<false>((a.flag & F_UEXPL) ? tY : tW, tY, lane);
     }
@@ -790,7 +870,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
 // Two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to that
 // bound cost no occupancy.
 template <int PP, typename S, bool OZ = false, int SPL = 1>
-__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 3) k_spmm_gram(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? (one_tile<PP, S, OZ>() ? 2 : 1) : 3) k_spmm_gram(const PassArgs a) {
   d_spmm_gram<PP, S, OZ, SPL>(a, blockIdx.x, gridDim.x);
 }
 
@@ -824,12 +904,13 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   using G = Geo<PP, S>;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
   constexpr bool OZG = oz_gram<PP, OZ>();
+  constexpr bool OT = one_tile<PP, S, OZ>();   // U read from global memory, four-product Gram
   // W^H W: three products where the applies take them, and in the p = 32 tensor-core pass
   // (whose Gram stays on the FP64 pipe); the p <= 16 tensor-core pass forms it there
-  constexpr bool M3G = M3A || (OZ && !OZG);
+  constexpr bool M3G = (M3A && !OT) || (OZ && !OZG);
   C* mA = smem;
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
-  C* tW = tiles + warp * 2 * G::TILE;
+  C* tW = tiles + warp * (OT ? 1 : 2) * G::TILE;
   C* tU = tW + G::TILE;
   if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
@@ -846,9 +927,12 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(tW, blk<C>(a.Q), r0, n, p, lane);
-    load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
+    if constexpr (!OT) load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
-    if constexpr (OZ) {
+    if constexpr (OT) {
+      apply_full3_g<PP, true>(tW, tW, a.U + r0 * p, (int)min((int64_t)CHUNK, n - r0), Fac3(a.mats, M_ALPHA, p), p,
+                              lane);                                       // W_{m+1} = Q_m - U_m alpha'
+    } else if constexpr (OZ) {
       oz_apply_any<PP, true, true>(tW, tW, tU, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane, adig);
       if constexpr (M3G) {
         __syncwarp();
@@ -874,7 +958,7 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
 // FP64: two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to
 // that bound cost no occupancy.  The tensor-core variant keeps the compiler's own choice.
 template <int PP, typename S, bool OZ = false>
-__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 3) k_cocr_passA(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? (one_tile<PP, S, OZ>() ? 2 : 1) : 3) k_cocr_passA(const PassArgs a) {
   d_cocr_passA<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 template <int PP>
@@ -896,7 +980,8 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   const bool first = a.flag & 1;
   const bool uexpl = a.flag & F_UEXPL;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
-  constexpr bool M3G = m3_gram<PP, S>();
+  constexpr bool OT = one_tile<PP, S, OZ>();   // S and U read from global memory
+  constexpr bool M3G = m3_gram<PP, S>() && !OT;
   // staged factors (four-product forms): T packed (upper triangle), alpha'xi, beta'
   C* mT = smem;
   C* mAX = smem + tri_packed<PP>() * mat_parts<S>();
@@ -904,7 +989,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   C* tiles = smem + (M3A ? 0 : passC_mats_elems<PP, S>());
   // two tiles per warp: Q is stored as soon as it is formed and read back (from L2, by the
   // same threads) for the S update, so X, S and Q never need three tiles at once
-  C* b0 = tiles + warp * 2 * G::TILE;
+  C* b0 = tiles + warp * (OT ? 1 : 2) * G::TILE;
   C* b1 = b0 + G::TILE;
   uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
   if constexpr (G::MATS_SMEM && !M3A) {
@@ -917,6 +1002,47 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
   GramAcc<G::NTRI, S, M3G> g;
   g.init(G_SYM, p, lane);
+  if constexpr (OT) {
+    // one tile per warp (p = 32): the same updates, S_m and U_m streamed from global memory
+    for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
+      const int64_t r0 = c * CHUNK;
+      const int rows = (int)min((int64_t)CHUNK, n - r0);
+      load_tile<PP>(b0, a.W, r0, n, p, lane);
+      __syncwarp();
+      tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);   // Q_{m+1}
+      __syncwarp();
+      store_tile<PP>(a.Q, b0, r0, n, p, lane);
+      if (!first) {
+        __syncwarp();
+        load_tile<PP>(b0, a.X, r0, n, p, lane);
+        __syncwarp();
+        apply_full3_g<PP, false>(b0, b0, a.S + r0 * p, rows, Fac3(a.mats, M_ALPHAXI, p), p, lane);   // X_{m+1}
+        __syncwarp();
+        store_tile<PP>(a.X, b0, r0, n, p, lane);
+        __syncwarp();
+        load_tile<PP>(b0, a.Q, r0, n, p, lane);   // Q_{m+1}, just stored
+        __syncwarp();
+        apply_full3_g<PP, false>(b0, b0, a.S + r0 * p, rows, Fac3(a.mats, M_BETA, p), p, lane);   // S_{m+1}
+      }
+      __syncwarp();
+      store_tile<PP>(a.S, b0, r0, n, p, lane);       // (setup: S_0 = Q_0)
+      __syncwarp();
+      if (uexpl) continue;
+      load_tile<PP>(b0, a.V, r0, n, p, lane);
+      __syncwarp();
+      if (!first) {
+        apply_full3_g<PP, false>(b0, b0, a.U + r0 * p, rows, Fac3(a.mats, M_BETA, p), p, lane);   // U_{m+1}
+        __syncwarp();
+      }
+      g.template add<false>(b0, b0, lane);
+      store_tile<PP>(a.U, b0, r0, n, p, lane);
+      __syncwarp();
+    }
+    if (uexpl) return;
+    __syncthreads();
+    cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+    return;
+  }
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
@@ -989,8 +1115,10 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   __syncthreads();
   cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
 }
+// Registers bounded to what 3 CTAs per SM allow (2 for the one-tile pass at p = 32), which
+// the shared memory also allows; left free the compiler takes about 220 at p = 16.
 template <int PP, typename S, bool OZ = false>
-__global__ void __launch_bounds__(NWARP * 32) k_cocr_passC(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, one_tile<PP, S, OZ>() ? 2 : 3) k_cocr_passC(const PassArgs a) {
   d_cocr_passC<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 // The tensor-core pass C: up to p = 16 its shared memory allows 3 CTAs per SM, and so does
@@ -1200,14 +1328,18 @@ __global__ void __launch_bounds__(NWARP * 32) k_cocg_pass2(const PassArgs a) {
 
 // CholQR2, second pass (the thin QR of Sec. 2.2 with one re-orthogonalisation): the
 // first Cholesky factor's T1 is applied to W in place (W <- Q1 = W T1, stored) and the
-// Gram Q1^H Q1 is formed for the second factor.  Partials: [Q1^H Q1 tri].
+// Gram Q1^H Q1 is formed for the second factor.  flag & F_SYM2 (bl_cocg_rq): also the
+// unconjugated Q1^T Q1, from which the stage after it forms Q^T Q of the final basis (a
+// well-conditioned block, unlike the W the first factor came from).  The shifted-CholQR3
+// fallback runs this pass twice.  Partials: [Q1^H Q1 tri] (+ [Q1^T Q1 tri]).
 template <int PP, typename S>
 __device__ __forceinline__ void d_qr2(const PassArgs& a, const int vblk, const int vgrid) {
   using C = typename Cx<S>::T;
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   constexpr bool M3A = m3_apply<PP, S>();
-  constexpr bool M3G = m3_gram<PP, S>();
+  constexpr bool M3G = qr2_m3<PP, S>();
+  const bool sym2 = a.flag & F_SYM2;
   C* mT = smem;
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
   C* tW = tiles + warp * (M3G ? 2 : 1) * G::TILE;
@@ -1219,6 +1351,9 @@ __device__ __forceinline__ void d_qr2(const PassArgs& a, const int vblk, const i
   Fac<PP, S> T{G::MATS_SMEM ? mT : reinterpret_cast<const C*>(a.mats + M_TINV * PMAX * PMAX), p};
   GramAcc<G::NTRI, S, M3G> g;
   g.init(G_HERM, p, lane);
+  constexpr bool M3S = M3G;
+  GramAcc<G::NTRI, S, M3S> gs;
+  gs.init(G_SYM, p, lane);
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);
@@ -1229,11 +1364,17 @@ __device__ __forceinline__ void d_qr2(const PassArgs& a, const int vblk, const i
     __syncwarp();
     if constexpr (M3G) g.template add3<true>(tW, tSD, lane);
     else g.template add<true>(tW, tW, lane);
+    if (sym2) {
+      if constexpr (M3S) gs.template add3<false>(tW, tSD, lane);
+      else gs.template add<false>(tW, tW, lane);
+    }
     store_tile<PP>(blk<C>(a.W), tW, r0, n, p, lane);
     __syncwarp();
   }
   __syncthreads();
-  cta_write_gram(g, reinterpret_cast<double2*>(tiles), a.partials + (int64_t)vblk * a.ne, warp, lane);
+  double2* out = a.partials + (int64_t)vblk * a.ne;
+  cta_write_gram(g, reinterpret_cast<double2*>(tiles), out, warp, lane);
+  if (sym2) cta_write_gram(gs, reinterpret_cast<double2*>(tiles), out + tri_count(p), warp, lane);
 }
 template <int PP, typename S>
 __global__ void __launch_bounds__(NWARP * 32) k_qr2(const PassArgs a) {
@@ -1277,7 +1418,8 @@ constexpr size_t pass_smem(int kind) {
                               kind == K_COCG_2);
   const bool oz_cocg = OZ && (kind == K_COCG_1 || kind == K_COCG_2);
   const bool m3 = (m3_apply<PP, S>() && !oz_kind) || oz_cocg;   // oz_cocg: no staged factors either
-  const int nt = (kind == K_QR2 && m3_gram<PP, S>()) ? 2 : (oz_cocg ? 2 : ntiles[kind]);
+  const bool ot = one_tile<PP, S, OZ>() && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C);
+  const int nt = (kind == K_QR2 && qr2_m3<PP, S>()) ? 2 : ((oz_cocg ? 2 : ntiles[kind]) / (ot ? 2 : 1));
   const size_t mats =
       m3 ? 0 : (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
   size_t s = mats + (size_t)NWARP * nt * tile;

@@ -408,10 +408,11 @@ __device__ void gstore_cols(double2* mats, int sl, const double2* s, int p, int 
 // the shift of shifted CholQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa), which
 // makes the factorisation succeed for any W of condition below about u^-1; the two
 // Cholesky QR passes that complete it then run (ctrl->qr_fb = 2, stage d_small_chol_fb).
-__device__ bool chol_gram(SmallShared& S, int p, Ctrl* ctrl) {
+// Returns 0 (failed: breakdown), 1 (plain Cholesky QR) or 2 (shifted: fallback started).
+__device__ int chol_gram(SmallShared& S, int p, Ctrl* ctrl) {
   expand_tri(S.gs, S.m[0], p, true);
-  if (chol_upper(S.m[0], S.m[1], p, S.red)) return true;
-  if (!BLCOC_LD(&ctrl->qr_fb_on) || !(ctrl->qr_shift > 0.0)) return false;
+  if (chol_upper(S.m[0], S.m[1], p, S.red)) return 1;
+  if (!BLCOC_LD(&ctrl->qr_fb_on) || !(ctrl->qr_shift > 0.0)) return 0;
   expand_tri(S.gs, S.m[0], p, true);
   if (threadIdx.x == 0) {
     double tr = 0.0;
@@ -423,10 +424,10 @@ __device__ bool chol_gram(SmallShared& S, int p, Ctrl* ctrl) {
   __syncthreads();
   for (int j = threadIdx.x; j < p; j += blockDim.x) S.m[0][j * LD + j].x += sh;
   __syncthreads();
-  if (!chol_upper(S.m[0], S.m[1], p, S.red)) return false;
+  if (!chol_upper(S.m[0], S.m[1], p, S.red)) return 0;
   if (threadIdx.x == 0) ctrl->qr_fb = 2;
   __syncthreads();
-  return true;
+  return 2;
 }
 
 // Setup after the residual pass: ||B||_F, Q_0 xi_0 = R_0 (Cholesky QR), T_0 = xi_0^{-1};
@@ -470,7 +471,8 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
     }
     return;
   }
-  if (!chol_gram(S, p, ctrl)) {
+  const int qr = chol_gram(S, p, ctrl);
+  if (qr == 0) {
     if (threadIdx.x == 0) { ctrl->done = 3; ctrl->bd_code = 1; }
     return;
   }
@@ -480,10 +482,7 @@ __device__ __noinline__ void d_small_setup(SmallShared& S, int p, int method, co
   emit_oz(oz, OZ_T, S.m[2], p, S.colexp);
   if (method == 0) {
     expand_tri(S.gs + 2 * E, S.m[3], p, false);
-    if (qr2) {   // G_QQ needs the final factor: the second stage forms it from R^T R
-      gstore(slot(mats, M_G1), S.m[3], p);
-      return;
-    }
+    if (qr2 || qr == 2) return;   // G_QQ needs the final basis: the last second-factor stage forms it
     matmul(S.m[4], S.m[2], true, S.m[3], false, p);   // T^T G
     matmul(S.m[5], S.m[4], false, S.m[2], false, p);  // (T^T G) T
     gstore(slot(mats, M_H), S.m[5], p);
@@ -575,7 +574,8 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
     __syncthreads();
     return;
   }
-  if (!chol_gram(S, p, ctrl)) {
+  const int qr = chol_gram(S, p, ctrl);
+  if (qr == 0) {
     if (threadIdx.x == 0) {
       ctrl->done = 3;
       ctrl->bd_code = 3;
@@ -593,10 +593,7 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   if (method == 0) {
     const int E = tri_count(p);
     expand_tri(S.gs + 2 * E, S.m[0], p, false);       // W^T W
-    if (qr2) {   // G_QQ+ and beta' need the final factor: the second stage forms them
-      gstore(slot(mats, M_G1), S.m[0], p);
-      return;
-    }
+    if (qr2 || qr == 2) return;   // G_QQ+ and beta' need the final basis: the last second-factor stage forms them
     matmul(S.m[3], S.m[2], true, S.m[0], false, p);   // T^T (W^T W)
     matmul(S.m[0], S.m[3], false, S.m[2], false, p);  // G_QQ+ = T^T W^T W T
     matmul(S.m[4], S.m[1], true, S.m[0], false, p);   // tau^T G_QQ+
@@ -611,13 +608,14 @@ __device__ __noinline__ void d_small_chol(SmallShared& S, int p, int method, con
   }
 }
 
-// CholQR2, second factor (after the pass W <- Q1 = W T1, Gram Q1^H Q1): tau2, T2 with
-// tau2^H tau2 = Q1^H Q1; the QR factor becomes tau = tau2 tau1 and the passes that follow
-// apply T2 to the stored Q1.  Iteration: xi_{m+1} <- tau2 xi_{m+1} (the first stage applied
-// tau1).  Setup (setup = 1): xi_0 = tau.  cocg also forms G_QQ (setup) or G_QQ+ and beta'
-// (iteration) from W^T W with the whole factor T1 T2.
+// CholQR2, second factor (after the pass W <- Q1 = W T1, Grams Q1^H Q1 and, for cocg,
+// Q1^T Q1): tau2, T2 with tau2^H tau2 = Q1^H Q1; the QR factor becomes tau = tau2 tau1 and
+// the passes that follow apply T2 to the stored Q1.  Iteration: xi_{m+1} <- tau2 xi_{m+1}
+// (the first stage applied tau1).  Setup (setup = 1): xi_0 = tau.  cocg, on the last such
+// stage (last = 1; the shifted-CholQR3 fallback has two): G_QQ (setup) or G_QQ+ and beta'
+// (iteration) from T2^T (Q1^T Q1) T2.
 __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, const double* stage1, int ncomp,
-                                           double2* mats, Ctrl* ctrl, int setup, uint2* oz) {
+                                           double2* mats, Ctrl* ctrl, int setup, uint2* oz, int last = 1) {
   if (BLCOC_LD(&ctrl->done)) return;
   sum_stage1(stage1, ncomp, S.gs);
   expand_tri(S.gs, S.m[0], p, true);                   // Q1^H Q1
@@ -640,12 +638,12 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
     matmul(S.m[3], S.m[1], false, S.m[5], false, p);   // xi <- tau2 xi
     gstore(slot(mats, M_XI), S.m[3], p);
   }
-  if (method == 0) {
-    gload(S.m[5], slot(mats, M_TINV), p);                   // T1
-    matmul(S.m[3], S.m[5], false, S.m[2], false, p);   // T1 T2
-    gload(S.m[0], slot(mats, M_G1), p);                     // W^T W (R^T R at setup)
-    matmul(S.m[5], S.m[3], true, S.m[0], false, p);
-    matmul(S.m[0], S.m[5], false, S.m[3], false, p);  // (T1 T2)^T G (T1 T2)
+  if (method == 0 && last) {
+    // Q^T Q of the final basis Q = Q1 T2 from the pass's unconjugated Gram Q1^T Q1 (Q1 is
+    // well conditioned, so no cond(W)^2 loss)
+    expand_tri(S.gs + 2 * tri_count(p), S.m[3], p, false);
+    matmul(S.m[5], S.m[2], true, S.m[3], false, p);
+    matmul(S.m[0], S.m[5], false, S.m[2], false, p);  // T2^T (Q1^T Q1) T2
     if (setup) {
       gstore(slot(mats, M_H), S.m[0], p);                   // G_QQ
     } else {
@@ -671,8 +669,9 @@ __device__ __noinline__ void d_small_chol2(SmallShared& S, int p, int method, co
 // QR is judged: a diagonal entry below 1e-14 of the largest is a breakdown.
 __device__ __noinline__ void d_small_chol_fb(SmallShared& S, int p, int method, const double* stage1, int ncomp,
                                              double2* mats, Ctrl* ctrl, int setup, uint2* oz) {
-  if (BLCOC_LD(&ctrl->done) || BLCOC_LD(&ctrl->qr_fb) == 0) return;
-  d_small_chol2(S, p, method, stage1, ncomp, mats, ctrl, setup, oz);
+  const int fb = BLCOC_LD(&ctrl->qr_fb);
+  if (BLCOC_LD(&ctrl->done) || fb == 0) return;
+  d_small_chol2(S, p, method, stage1, ncomp, mats, ctrl, setup, oz, fb == 1);
   __syncthreads();
   if (threadIdx.x == 0) {
     const int left = ctrl->qr_fb - 1;

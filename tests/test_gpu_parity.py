@@ -230,10 +230,10 @@ def test_breakdown_on_nearly_dependent_columns_agrees_with_oracle(method, gap, e
 
 def test_shifted_cholqr3_fallback_on_ill_conditioned_right_hand_sides():
     """Columns dependent to 1e-10: a Cholesky QR cannot resolve them (cond^2 eps >> 1), a
-    Householder QR can.  The oracle (Householder) converges.  bl_cocr_rq with the shifted
-    CholQR3 fallback (default) converges to the tolerance as well and its QR factor xi_0
-    matches the oracle's where it is resolved; without the fallback, and for bl_cocg_rq
-    (which has none), the solve reports a breakdown at the setup QR."""
+    Householder QR can.  The oracle (Householder) converges.  Both rq methods with the
+    shifted CholQR3 fallback (default) converge to the tolerance as well and their QR factor
+    xi_0 matches the oracle's where it is resolved; without the fallback the solve reports
+    a breakdown at the setup QR."""
     torch = need_gpu()
     from paper_1601_05362_gb300 import blcoc
     A = P.random_complex_symmetric(600, 8, seed=41, diag=3.0 + 0.6j, scale=0.25)
@@ -244,19 +244,18 @@ def test_shifted_cholqr3_fallback_on_ill_conditioned_right_hand_sides():
     ref0 = O.bl_cocr_rq(A.to_scipy(), Bh, tol=0.0, maxit=0)
     B = to_dev(torch, Bh)
     h = _handle(A)
-    X = torch.zeros_like(B)
-    assert h.solve(B, X, method="cocr_rq", tol=0.0, maxit=0) == blcoc.BLCOC_NOT_CONVERGED, h.last_error()
-    d_gpu, d_ref = np.abs(np.diag(h.xi(4))), np.abs(np.diag(ref0.xi))
-    assert np.max(np.abs(d_gpu - d_ref) / d_ref) < 1e-4, (d_gpu, d_ref)
-    X.zero_()
-    assert h.solve(B, X, method="cocr_rq", tol=1e-10, maxit=500) == blcoc.BLCOC_OK, h.last_error()
-    assert O.true_relres(A.to_scipy(), Bh, X.cpu().numpy()) <= 1e-9
-    h.set_option("qr_fallback", 0)
-    X.zero_()
-    assert h.solve(B, X, method="cocr_rq", tol=1e-10, maxit=500) == blcoc.BLCOC_BREAKDOWN
-    h.set_option("qr_fallback", 1)
-    X.zero_()
-    assert h.solve(B, X, method="cocg_rq", tol=1e-10, maxit=500) == blcoc.BLCOC_BREAKDOWN
+    for method in ("cocr_rq", "cocg_rq"):
+        h.set_option("qr_fallback", 1)
+        X = torch.zeros_like(B)
+        assert h.solve(B, X, method=method, tol=0.0, maxit=0) == blcoc.BLCOC_NOT_CONVERGED, h.last_error()
+        d_gpu, d_ref = np.abs(np.diag(h.xi(4))), np.abs(np.diag(ref0.xi))
+        assert np.max(np.abs(d_gpu - d_ref) / d_ref) < 1e-4, (method, d_gpu, d_ref)
+        X.zero_()
+        assert h.solve(B, X, method=method, tol=1e-10, maxit=500) == blcoc.BLCOC_OK, (method, h.last_error())
+        assert O.true_relres(A.to_scipy(), Bh, X.cpu().numpy()) <= 1e-9
+        h.set_option("qr_fallback", 0)
+        X.zero_()
+        assert h.solve(B, X, method=method, tol=1e-10, maxit=500) == blcoc.BLCOC_BREAKDOWN
     h.close()
 
 
