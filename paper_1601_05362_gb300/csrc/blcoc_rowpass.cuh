@@ -262,6 +262,12 @@ constexpr bool one_tile() { return PP >= 32 && sizeof(S) == 8 && !OZ; }
 // of 64 x 64 real entries per warp would not fit beside the tiles).
 template <int PP, bool OZ>
 constexpr bool oz_gram() { return OZ && PP <= 16; }
+// The tensor-core kernel set's SpMM: the tensor-core variant (T apply, W^T Y Gram on the
+// tensor cores) up to p = 16; at p = 32 the FP64 one-tile SpMM, which is faster there
+// (17.7 against 22.5 ms on the 128^3 problem) because only its triangular T apply would
+// run on the tensor cores.
+template <int PP>
+constexpr bool oz_spmm() { return PP <= 16; }
 
 // Per-warp shared-memory buffer of the p = 32 tensor-core applies (A digit fragments of
 // one 16-row tile), in uint4 units; 0 where the applies split in registers.
@@ -1560,8 +1566,8 @@ void prepare_pass_kernels_tc() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || done[dev]) return;
-  cudaFuncSetAttribute(k_spmm_gram<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<PP, double, true>(K_SPMM_GRAM));
+  cudaFuncSetAttribute(k_spmm_gram<PP, double, oz_spmm<PP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double, oz_spmm<PP>()>(K_SPMM_GRAM));
   cudaFuncSetAttribute(k_cocr_passA_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_A));
   cudaFuncSetAttribute(k_cocr_passC_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1570,16 +1576,23 @@ void prepare_pass_kernels_tc() {
                        (int)pass_smem<PP, double, true>(K_COCG_1));
   cudaFuncSetAttribute(k_cocg_pass2_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCG_2));
-  set_spmm_split_smem<PP, double, true, 2>();
-  set_spmm_split_smem<PP, double, true, 4>();
+  set_spmm_split_smem<PP, double, oz_spmm<PP>(), 2>();
+  set_spmm_split_smem<PP, double, oz_spmm<PP>(), 4>();
   done[dev] = true;
+}
+
+// Launch-grid rule of the tensor-core set: the SpMM's from its own kernel (see oz_spmm).
+template <int PP>
+int pass_grid_tc(int64_t n, int kind, int num_sms) {
+  if (kind == K_SPMM_GRAM && !oz_spmm<PP>()) return pass_grid<PP, double, false>(n, kind, num_sms);
+  return pass_grid<PP, double, true>(n, kind, num_sms);
 }
 
 template <int PP>
 const KernelSet& kernel_set_tc() {
   static const KernelSet ks = {
       &launch_pass<PP, double, K_RESID, k_resid<PP, double>>,
-      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>, true>,
+      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, oz_spmm<PP>()>, oz_spmm<PP>()>,
       &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
       &launch_pass<PP, double, K_COCR_A, k_cocr_passA_tc<PP>, true>,
       &launch_pass<PP, double, K_COCR_C, k_cocr_passC_tc<PP>, true>,
@@ -1587,9 +1600,9 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2_tc<PP>, true>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
       &launch_pass<PP, double, K_QR2, k_qr2<PP, double>>,
-      spmm_split_fn<PP, double, true, 2>(),
-      spmm_split_fn<PP, double, true, 4>(),
-      &pass_grid<PP, double, true>,
+      spmm_split_fn<PP, double, oz_spmm<PP>(), 2>(),
+      spmm_split_fn<PP, double, oz_spmm<PP>(), 4>(),
+      &pass_grid_tc<PP>,
       &prepare_pass_kernels_tc<PP>,
   };
   return ks;
