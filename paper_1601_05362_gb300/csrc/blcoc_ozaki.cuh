@@ -135,6 +135,41 @@ __device__ __forceinline__ void oz_mma(float (&c)[4], const unsigned (&a)[4], ui
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
+// Exact integer value of a level sum.  K: the longest dot product behind it.  A level sums
+// at most 8 slice pairs, so |sum| <= 8 K 127^2; below 2^22 (K <= 32) it is read through the
+// 1.5 2^23 constant on the FP32 and integer pipes, above that by a conversion.
+template <int K>
+__device__ __forceinline__ int oz_level_int(float f) {
+  if constexpr (8 * K * 127 * 127 < (1 << 22)) return __float_as_int(f + 12582912.0f) - 0x4B400000;
+  else return __float2int_rn(f);
+}
+
+// One output from its nine exact level sums: value = sum_L acc_L 2^(E - 7L), E = e_r + f_c
+// (the row and column scalings).  W = value 2^(53 - E) is formed as a 64-bit integer:
+// levels 2..7 exactly (|W| < 2^62.02), levels 8..10 summed in FP32 and rounded to an
+// integer (error below one unit of W, 2^(E - 53), against the 2^(E - 56) truncation of
+// every one of the K operand pairs).  One conversion to double, then the scaling by 2^(E - 53)
+// as an add to the exponent field: a single operation on the FP64 pipe instead of five.
+template <int K>
+__device__ __forceinline__ double oz_value(const float (&acc)[OZ_NLEV][4], int o, int E) {
+  static_assert(OZ_NLEV == 9 && OZ_DB == 7, "the integer frame below is laid out for levels 2..10 of 7-bit digits");
+  const int a = oz_level_int<K>(acc[0][o]) * 128 + oz_level_int<K>(acc[1][o]);   // levels 2, 3: weight 2^32
+  const int b = oz_level_int<K>(acc[2][o]) * 128 + oz_level_int<K>(acc[3][o]);   // levels 4, 5: 2^18
+  const int c = oz_level_int<K>(acc[4][o]) * 128 + oz_level_int<K>(acc[5][o]);   // levels 6, 7: 2^4
+  // levels 8..10 (weights 2^-3, 2^-10, 2^-17): |t| < 2^23.02, t / 8 rounded to an integer
+  const float t = fmaf(acc[8][o], 0x1p-14f, fmaf(acc[7][o], 0x1p-7f, acc[6][o]));
+  const int d = __float_as_int(fmaf(t, 0.125f, 12582912.0f)) - 0x4B400000;
+  const long long w = (long long)a * 4294967296ll + (long long)b * 262144ll + (long long)c * 16ll + d;
+  double v = (double)w;
+  const int s = E - 53;
+  if (s >= -1022 && s <= 960) {   // |v| in [1, 2^63] when w != 0: the scaled value stays normal
+    if (w != 0) v = __hiloint2double(__double2hiint(v) + (int)((unsigned)s << 20), __double2loint(v));
+  } else {
+    v = ldexp(v, s);
+  }
+  return v;
+}
+
 // Recombination of the four outputs one lane holds for n-tile nt of an m-tile
 // ((ra, 8nt+2q), (ra, 8nt+2q+1), (rb, 8nt+2q), (rb, 8nt+2q+1)) from their nine exact level
 // sums, and their write to `out` (added to / subtracted from `base`).
@@ -145,21 +180,13 @@ __device__ __forceinline__ void oz_store_outputs(double2* out, const double2* ba
   auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
-    long long hi = 0, lo = 0;
-#pragma unroll
-    for (int L = 2; L <= 6; ++L) hi += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (6 - L));
-#pragma unroll
-    for (int L = 7; L <= OZ_LMAX; ++L) lo += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (10 - L));
     const int row = (o < 2) ? ra : rb;
     const int col = 8 * nt + 2 * q + (o & 1);
     const int ebr = (o < 2) ? eba : ebb;
     const int ebc = __ldg(colexp + col);
-    // value = (hi 2^-42 + lo 2^-70) 2^(e_r + f_c), e = eb - 1022
-    const int sc = (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022) - 42;
-    double v = fma((double)lo, 0x1p-28, (double)hi);
+    // e = eb - 1022 for the row and the column
+    double v = oz_value<2 * PP>(acc, o, (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022));
     if (ebr == 2047 || ebc == 2047) v = __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
-    else if (sc >= -1020 && sc <= 1020) v *= __longlong_as_double((long long)(sc + 1023) << 52);
-    else v = ldexp(v, sc);
     const int kc = col % PP;
     if (kc < p) {
       double2 cur = BASE ? base[tx(kc, row)] : make_double2(0.0, 0.0);
@@ -386,18 +413,10 @@ __device__ __forceinline__ double oz_tile_val(const double2* T, int p, int r, in
   return m >= PP ? v.y : v.x;
 }
 
-// exact level sums -> double: value = (hi 2^-42 + lo 2^-70) 2^(e_r + f_c), e = eb - 1022
+// exact level sums of a Gram entry (K = the chunk's 32 rows) -> double, e = eb - 1022
 __device__ __forceinline__ double oz_recombine(const float (&acc)[OZ_NLEV][4], int o, int ebr, int ebc) {
-  long long hi = 0, lo = 0;
-#pragma unroll
-  for (int L = 2; L <= 6; ++L) hi += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (6 - L));
-#pragma unroll
-  for (int L = 7; L <= OZ_LMAX; ++L) lo += (long long)__float2int_rn(acc[L - 2][o]) << (OZ_DB * (10 - L));
-  const int sc = (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022) - 42;
-  double v = fma((double)lo, 0x1p-28, (double)hi);
   if (ebr == 2047 || ebc == 2047) return __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
-  if (sc >= -1020 && sc <= 1020) return v * __longlong_as_double((long long)(sc + 1023) << 52);
-  return ldexp(v, sc);
+  return oz_value<32>(acc, o, (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022));
 }
 
 // sums[tile][o][lane] += P of this chunk (Y, Z: swizzled [k][32] tiles; SAME: Z is Y).
