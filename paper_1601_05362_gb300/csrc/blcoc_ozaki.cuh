@@ -15,10 +15,10 @@
 // Recombination: the nine exact level sums are combined as two 64-bit integers and turned
 // into a double with two conversions and two FMAs, added to the base value.
 //
-// The p x p stage kernels write each factor already split, in the B-fragment order of
-// mma.m16n8k16 (`oz_emit_factor`); the row passes split X' in registers (`oz_apply`,
-// p <= 16) or, at p = 32 where eight slices of four k16 steps would not fit in registers,
-// into a per-warp shared-memory buffer one 16-row tile at a time (`oz_apply_sm`).
+// The p x p stage kernels write each factor already split (`oz_emit_factor`); the row
+// passes split X' in registers: 16 rows at a time as the A operand up to p = 16
+// (`oz_apply`), and at p = 32, where eight slices of four k16 steps of 16 rows would not
+// fit, transposed (Y'^T = M'^T X'^T) with 8 rows at a time as the B operand (`oz_apply_t`).
 #pragma once
 
 #include "blcoc_common.cuh"
@@ -87,10 +87,15 @@ __device__ __forceinline__ double oz_mbig(const double2* M, int ld, int p, int k
   return v.x;
 }
 
-// Split a p x p factor into OZ_NSL bf16 slices in the B-fragment order of mma.m16n8k16
-// (row.col): frag[((t*KS + ks)*NT + nt)*32 + lane] = {rows 16ks+2q, +1 ; rows +8, +9} of
-// column 8nt + g, g = lane/4, q = lane%4.  colexp[j]: largest biased exponent in column j
-// of M'.  All threads of the CTA call this; it synchronises internally.
+// Split a p x p factor into OZ_NSL bf16 slices.  Up to p = 16, in the B-fragment order of
+// mma.m16n8k16 (row.col): frag[((t*KS + ks)*NT + nt)*32 + lane] = {rows 16ks+2q, +1 ; rows
+// +8, +9} of column 8nt + g, g = lane/4, q = lane%4.  At p = 32, where the row passes
+// multiply transposed (Y'^T = M'^T X'^T, oz_apply_t), in the A-fragment order of M'^T:
+// frag4[((t*KS + ks)*MT + mt)*32 + lane] = the four registers {A[m0][k0], A[m0][k0+1]},
+// {A[m1][k0], A[m1][k0+1]}, {A[m0][k0+8], A[m0][k0+9]}, {A[m1][k0+8], A[m1][k0+9]} with
+// A[m][k] = M'[k][m], m0 = 16mt + g, m1 = m0 + 8, k0 = 16ks + 2q.  colexp[j]: largest
+// biased exponent in column j of M'.  All threads of the CTA call this; it synchronises
+// internally.
 template <int PP>
 __device__ void oz_emit_factor(const double2* M, int ld, int p, uint2* __restrict__ frag, int* __restrict__ colexp,
                                int* sh_colexp) {
@@ -102,6 +107,36 @@ __device__ void oz_emit_factor(const double2* M, int ld, int p, uint2* __restric
     colexp[j] = eb;
   }
   __syncthreads();
+  if constexpr (PP >= 32) {
+    constexpr int MT = G::NR / 16;
+    uint4* frag4 = reinterpret_cast<uint4*>(frag);
+    for (int w = threadIdx.x; w < G::KS * MT * 32; w += blockDim.x) {
+      const int lane = w & 31, mt = (w >> 5) % MT, ks = (w >> 5) / MT;
+      const int g = lane >> 2, q = lane & 3;
+      const int m0 = 16 * mt + g, m1 = m0 + 8, k0 = 16 * ks + 2 * q;
+      const int km[8] = {k0, k0 + 1, k0, k0 + 1, k0 + 8, k0 + 9, k0 + 8, k0 + 9};
+      const int mm[8] = {m0, m0, m1, m1, m0, m0, m1, m1};
+      unsigned long long F[8];
+      unsigned sg[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const double v = oz_mbig<PP>(M, ld, p, km[r], mm[r]);
+        F[r] = oz_fixed(v, sh_colexp[mm[r]]);
+        sg[r] = (__double_as_longlong(v) < 0) ? 1u : 0u;
+      }
+#pragma unroll
+      for (int t = 1; t <= OZ_NSL; ++t) {
+        const int shft = 56 - OZ_DB * t;
+        unsigned h[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) h[r] = oz_bf16((unsigned)((F[r] >> shft) & 127ull), sg[r]);
+        frag4[((t - 1) * G::KS + ks) * MT * 32 + mt * 32 + lane] =
+            make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+      }
+    }
+    __syncthreads();
+    return;
+  }
   for (int w = threadIdx.x; w < G::KS * G::NT * 32; w += blockDim.x) {
     const int lane = w & 31, nt = (w >> 5) % G::NT, ks = (w >> 5) / G::NT;
     const int g = lane >> 2, q = lane & 3, j = 8 * nt + g;
@@ -281,91 +316,116 @@ __device__ __forceinline__ void oz_apply(double2* out, const double2* base, cons
   }
 }
 
-// Digit fragments of the A operand (X' rows ra = 16 mt + g and rb = ra + 8, real columns
-// 16 ks + {2q, 2q+1, 2q+8, 2q+9}) of one 16-row tile, written to the warp's buffer
-// adig[(t * KS + ks) * 32 + lane] (uint4: the four A registers of slice t, k-step ks).
-template <int PP>
-__device__ __forceinline__ void oz_split_rows_to_smem(uint4* adig, const double2* in, int p, int ra, int rb, int eba,
-                                                      int ebb, int lane) {
+// out = base (+/-) in * M for the warp's 32-row chunk at p = 32, computed transposed,
+// Y'^T = M'^T X'^T, one 8-row group at a time: the group's rows are the B operand
+// (k16 x n8), so a lane holds the digits of its row g's real columns 16 ks + {2q, 2q+1,
+// 2q+8, 2q+9} for all four k-steps in registers (8 slices x 4 k-steps x 2 registers), and
+// the factor's slices are the A operand, read per use from its fragment buffer (A-fragment
+// order of M'^T, oz_emit_factor).  Same slicing, same levels, same exactness as oz_apply.
+// GIN: `in` is read from global memory (in_g = the chunk's first row of a row-major n x p
+// block, `rows` of them inside n, the rest zero) instead of a swizzled tile.  `out` may
+// alias `base` or `in` (a group's rows are all read before any of them is written).
+template <int PP, bool SUB, bool BASE, bool GIN>
+__device__ __forceinline__ void oz_apply_t(double2* out, const double2* base, const double2* in,
+                                           const double2* __restrict__ in_g, int rows,
+                                           const uint4* __restrict__ frag, const int* __restrict__ colexp, int p,
+                                           int lane) {
   using G = OzGeo<PP>;
+  static_assert(PP == 32, "the transposed exact-slice product is laid out for p = 32");
+  constexpr int MT = G::NR / 16;   // m16 tiles of output real columns
   auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
-  const int q = lane & 3;
-#pragma unroll 1
-  for (int ks = 0; ks < G::KS; ++ks) {
-    unsigned long long F[8];
-    unsigned sg[8];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int col = 16 * ks + 2 * q + (c & 1) + 8 * (c >> 1);
-      const int kc = col % PP;
-      const bool im = col >= PP;
-      double va = 0.0, vb = 0.0;
-      if (kc < p) {
-        const double2 xa = in[tx(kc, ra)], xb = in[tx(kc, rb)];
-        va = im ? xa.y : xa.x;
-        vb = im ? xb.y : xb.x;
-      }
-      F[2 * c] = oz_fixed(va, eba);
-      sg[2 * c] = (__double_as_longlong(va) < 0) ? 1u : 0u;
-      F[2 * c + 1] = oz_fixed(vb, ebb);
-      sg[2 * c + 1] = (__double_as_longlong(vb) < 0) ? 1u : 0u;
-    }
-#pragma unroll
-    for (int t = 0; t < OZ_NSL; ++t) {
-      const int shft = 56 - OZ_DB * (t + 1);
-      unsigned h[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) h[e] = oz_bf16((unsigned)((F[e] >> shft) & 127ull), sg[e]);
-      adig[(t * G::KS + ks) * 32 + lane] =
-          make_uint4(h[0] | (h[2] << 16), h[1] | (h[3] << 16), h[4] | (h[6] << 16), h[5] | (h[7] << 16));
-    }
-  }
-}
-
-// oz_apply with the A digits staged in shared memory (p = 32): `adig` is this warp's
-// buffer of OZ_NSL * KS * 32 uint4 (16 KB at p = 32).  Same arithmetic, same results.
-template <int PP, bool SUB, bool BASE>
-__device__ __forceinline__ void oz_apply_sm(double2* out, const double2* base, const double2* in,
-                                            const uint2* __restrict__ frag, const int* __restrict__ colexp, int p,
-                                            int lane, uint4* adig) {
-  using G = OzGeo<PP>;
-  auto tx = [](int k, int r) { return k * 32 + (r ^ (k & 7)); };
-  int eb_row = 0;
-  for (int k = 0; k < p; ++k) {
-    const double2 v = in[tx(k, lane)];
-    eb_row = max(eb_row, max(oz_bexp(v.x), oz_bexp(v.y)));
-  }
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll 1
-  for (int mt = 0; mt < 2; ++mt) {
-    const int ra = 16 * mt + g, rb = ra + 8;
-    const int eba = __shfl_sync(0xffffffffu, eb_row, ra), ebb = __shfl_sync(0xffffffffu, eb_row, rb);
-    __syncwarp();   // the previous tile's digits have been read
-    oz_split_rows_to_smem<PP>(adig, in, p, ra, rb, eba, ebb, lane);
-    __syncwarp();
+  for (int grp = 0; grp < CHUNK / 8; ++grp) {
+    const int row = 8 * grp + g;
+    // this lane's complex entries of its row: kc = 2q + {0, 1, 8, 9, 16, 17, 24, 25}
+    double2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int kc = 2 * q + (j & 1) + 8 * (j >> 1);
+      double2 x = make_double2(0.0, 0.0);
+      if (kc < p) {
+        if constexpr (GIN) {
+          if (row < rows) x = __ldg(in_g + (int64_t)row * p + kc);
+        } else {
+          x = in[tx(kc, row)];
+        }
+      }
+      v[j] = x;
+    }
+    // the row's exponent: its 64 real entries are spread over the four lanes of group g
+    int eb = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) eb = max(eb, max(oz_bexp(v[j].x), oz_bexp(v[j].y)));
+    eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 1));
+    eb = max(eb, __shfl_xor_sync(0xffffffffu, eb, 2));
+    // B fragments: k-step ks holds real columns 16 ks + {2q, 2q+1, 2q+8, 2q+9}: the real
+    // parts of v[0..3] (ks = 0) and v[4..7] (ks = 1), their imaginary parts (ks = 2, 3)
+    unsigned Bd[OZ_NSL][G::KS][2];
+#pragma unroll
+    for (int ks = 0; ks < G::KS; ++ks) {
+      unsigned long long F[4];
+      unsigned sg[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double2 x = v[(ks & 1) * 4 + c];
+        const double val = (ks >= 2) ? x.y : x.x;
+        F[c] = oz_fixed(val, eb);
+        sg[c] = (__double_as_longlong(val) < 0) ? 1u : 0u;
+      }
+#pragma unroll
+      for (int t = 0; t < OZ_NSL; ++t) {
+        const int shft = 56 - OZ_DB * (t + 1);
+        unsigned h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) h[c] = oz_bf16((unsigned)((F[c] >> shft) & 127ull), sg[c]);
+        Bd[t][ks][0] = h[0] | (h[1] << 16);
+        Bd[t][ks][1] = h[2] | (h[3] << 16);
+      }
+    }
+    // output rows 2q and 2q + 1 of the group: their exponents sit with lanes 8q and 8q + 4
+    const int ebn0 = __shfl_sync(0xffffffffu, eb, 8 * q), ebn1 = __shfl_sync(0xffffffffu, eb, 8 * q + 4);
+    __syncwarp();   // every lane has read the group's rows before any is written
 #pragma unroll 1
-    for (int nt = 0; nt < G::NT; ++nt) {
+    for (int mt = 0; mt < MT; ++mt) {
       float acc[OZ_NLEV][4];
 #pragma unroll
       for (int l = 0; l < OZ_NLEV; ++l) acc[l][0] = acc[l][1] = acc[l][2] = acc[l][3] = 0.f;
-#pragma unroll 1
+#pragma unroll
       for (int ks = 0; ks < G::KS; ++ks) {
-        uint2 Bf[OZ_NSL];
 #pragma unroll
-        for (int t = 0; t < OZ_NSL; ++t) Bf[t] = __ldg(frag + (t * G::KS + ks) * G::NT * 32 + nt * 32 + lane);
-#pragma unroll
-        for (int s = 1; s <= OZ_NSL; ++s) {
-          const uint4 a4 = adig[((s - 1) * G::KS + ks) * 32 + lane];
+        for (int t = 1; t <= OZ_NSL; ++t) {
+          const uint4 a4 = __ldg(frag + ((t - 1) * G::KS + ks) * MT * 32 + mt * 32 + lane);
           const unsigned A[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
-          for (int t = 1; t <= OZ_NSL; ++t) {
-            if (s + t > OZ_LMAX) continue;
-            oz_mma(acc[s + t - 2], A, Bf[t - 1]);
+          for (int s2 = 1; s2 <= OZ_NSL; ++s2) {
+            if (s2 + t > OZ_LMAX) continue;
+            oz_mma(acc[s2 + t - 2], A, make_uint2(Bd[s2 - 1][ks][0], Bd[s2 - 1][ks][1]));
           }
         }
       }
-      oz_store_outputs<PP, SUB, BASE>(out, base, acc, colexp, ra, rb, eba, ebb, nt, q, p);
+      // C fragment: (m0, 2q), (m0, 2q+1), (m0+8, 2q), (m0+8, 2q+1), m0 = 16 mt + g
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int m = 16 * mt + g + 8 * (o >> 1);
+        const int r = 8 * grp + 2 * q + (o & 1);
+        const int ebr = (o & 1) ? ebn1 : ebn0;
+        const int ebc = __ldg(colexp + m);
+        double vv = oz_value<2 * PP>(acc, o, (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022));
+        if (ebr == 2047 || ebc == 2047) vv = __longlong_as_double(0x7FF8000000000000ll);   // propagate inf/nan
+        const int kc = m % PP;
+        if (kc < p) {
+          double2 cur = BASE ? base[tx(kc, r)] : make_double2(0.0, 0.0);
+          double& dst = (m >= PP) ? cur.y : cur.x;
+          dst = SUB ? dst - vv : dst + vv;
+          // the real and imaginary halves of one complex output come from m-tiles mt and
+          // mt + MT/2: write only this half
+          if (m >= PP) out[tx(kc, r)].y = cur.y;
+          else out[tx(kc, r)].x = cur.x;
+        }
+      }
     }
+    __syncwarp();   // the group's writes land before the next group's reads (in-place use)
   }
 }
 

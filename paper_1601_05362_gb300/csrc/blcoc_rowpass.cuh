@@ -269,17 +269,28 @@ constexpr bool oz_gram() { return OZ && PP <= 16; }
 template <int PP>
 constexpr bool oz_spmm() { return PP <= 16; }
 
-// Per-warp shared-memory buffer of the p = 32 tensor-core applies (A digit fragments of
-// one 16-row tile), in uint4 units; 0 where the applies split in registers.
+// The tensor-core passes A and C at p = 32 keep one tile per warp, as the FP64 ones do:
+// the second operand of each block update is split into slice digits straight from global
+// memory (through L1), so that two CTAs fit an SM.
 template <int PP, bool OZ>
-constexpr int oz_adig_u4() { return (OZ && PP >= 32) ? OZ_NSL * OzGeo<PP>::KS * 32 : 0; }
+constexpr bool tc_one_tile() { return OZ && PP >= 32; }
 
 // out = base (+/-) in * M on the tensor cores, M given by its exact-slice fragments.
 template <int PP, bool SUB, bool BASE>
 __device__ __forceinline__ void oz_apply_any(double2* out, const double2* base, const double2* in, const uint2* fz,
-                                             int p, int lane, uint4* adig) {
-  if constexpr (PP >= 32) oz_apply_sm<PP, SUB, BASE>(out, base, in, fz, oz_colexp_of(fz), p, lane, adig);
+                                             int p, int lane) {
+  if constexpr (PP >= 32)
+    oz_apply_t<PP, SUB, BASE, false>(out, base, in, nullptr, 0, reinterpret_cast<const uint4*>(fz), oz_colexp_of(fz),
+                                     p, lane);
   else oz_apply<PP, SUB, BASE>(out, base, in, fz, oz_colexp_of(fz), p, lane);
+}
+// The same with `in` read from global memory (in_g = the chunk's first row, `rows` of them
+// inside n); p = 32 only.
+template <int PP, bool SUB, bool BASE>
+__device__ __forceinline__ void oz_apply_gin(double2* out, const double2* base, const double2* in_g, int rows,
+                                             const uint2* fz, int p, int lane) {
+  oz_apply_t<PP, SUB, BASE, true>(out, base, nullptr, in_g, rows, reinterpret_cast<const uint4*>(fz),
+                                  oz_colexp_of(fz), p, lane);
 }
 template <int PP, typename S>
 constexpr bool m3_gram() { return sizeof(S) == 8 && PP >= 8; }
@@ -836,7 +847,6 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   g.init(G_SYM, p, lane);
   constexpr bool OZG = oz_gram<PP, OZ>();
   double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
-  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
   if constexpr (OZG) {
     for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
   }
@@ -858,7 +868,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     __syncwarp();   // every lane has read Y for the Gram before the in-place apply
     if (applyT) {
       if constexpr (OZ) {
-        oz_apply_any<PP, false, false>(tY, nullptr, tY, a.oz + OZ_T * OZ_SLOT_U2, p, lane, adig);
+        oz_apply_any<PP, false, false>(tY, nullptr, tY, a.oz + OZ_T * OZ_SLOT_U2, p, lane);
       } else if constexpr (M3A) {
         tri_apply3_inplace<PP>(tY, Fac3(a.mats, M_TINV, p), p, lane);
       } else {
@@ -911,12 +921,13 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   constexpr bool M3A = m3_apply<PP, S, OZ>();
   constexpr bool OZG = oz_gram<PP, OZ>();
   constexpr bool OT = one_tile<PP, S, OZ>();   // U read from global memory, four-product Gram
-  // W^H W: three products where the applies take them, and in the p = 32 tensor-core pass
-  // (whose Gram stays on the FP64 pipe); the p <= 16 tensor-core pass forms it there
-  constexpr bool M3G = (M3A && !OT) || (OZ && !OZG);
+  constexpr bool OTZ = tc_one_tile<PP, OZ>();  // the same for the p = 32 tensor-core pass
+  // W^H W: three products where the applies take them and two tiles are kept; the p <= 16
+  // tensor-core pass forms it on the tensor cores
+  constexpr bool M3G = ((M3A && !OT) || (OZ && !OZG)) && !OTZ;
   C* mA = smem;
   C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
-  C* tW = tiles + warp * (OT ? 1 : 2) * G::TILE;
+  C* tW = tiles + warp * ((OT || OTZ) ? 1 : 2) * G::TILE;
   C* tU = tW + G::TILE;
   if constexpr (G::MATS_SMEM && !M3A) {
     load_mat<PP>(mA, a.mats + M_ALPHA * PMAX * PMAX, p);
@@ -926,20 +937,22 @@ __device__ __forceinline__ void d_cocr_passA(const PassArgs& a, const int vblk, 
   GramAcc<G::NTRI, S, M3G> g;
   g.init(G_HERM, p, lane);
   double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
-  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
   if constexpr (OZG) {
     for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
   }
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(tW, blk<C>(a.Q), r0, n, p, lane);
-    if constexpr (!OT) load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
+    if constexpr (!OT && !OTZ) load_tile<PP>(tU, blk<C>(a.U), r0, n, p, lane);
     __syncwarp();
-    if constexpr (OT) {
+    if constexpr (OTZ) {
+      oz_apply_gin<PP, true, true>(tW, tW, a.U + r0 * p, (int)min((int64_t)CHUNK, n - r0),
+                                   a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane);   // W_{m+1} = Q_m - U_m alpha'
+    } else if constexpr (OT) {
       apply_full3_g<PP, true>(tW, tW, a.U + r0 * p, (int)min((int64_t)CHUNK, n - r0), Fac3(a.mats, M_ALPHA, p), p,
                               lane);                                       // W_{m+1} = Q_m - U_m alpha'
     } else if constexpr (OZ) {
-      oz_apply_any<PP, true, true>(tW, tW, tU, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane, adig);
+      oz_apply_any<PP, true, true>(tW, tW, tU, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane);
       if constexpr (M3G) {
         __syncwarp();
         sd_tile<PP>(tU, tW, p, lane);                                         // U_m is no longer needed
@@ -987,7 +1000,8 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   const bool uexpl = a.flag & F_UEXPL;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
   constexpr bool OT = one_tile<PP, S, OZ>();   // S and U read from global memory
-  constexpr bool M3G = m3_gram<PP, S>() && !OT;
+  constexpr bool OTZ = tc_one_tile<PP, OZ>();  // the same for the p = 32 tensor-core pass
+  constexpr bool M3G = m3_gram<PP, S>() && !OT && !OTZ;
   // staged factors (four-product forms): T packed (upper triangle), alpha'xi, beta'
   C* mT = smem;
   C* mAX = smem + tri_packed<PP>() * mat_parts<S>();
@@ -995,9 +1009,8 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   C* tiles = smem + (M3A ? 0 : passC_mats_elems<PP, S>());
   // two tiles per warp: Q is stored as soon as it is formed and read back (from L2, by the
   // same threads) for the S update, so X, S and Q never need three tiles at once
-  C* b0 = tiles + warp * (OT ? 1 : 2) * G::TILE;
+  C* b0 = tiles + warp * ((OT || OTZ) ? 1 : 2) * G::TILE;
   C* b1 = b0 + G::TILE;
-  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, OZ>();
   if constexpr (G::MATS_SMEM && !M3A) {
     load_mat_tri<PP>(mT, a.mats + M_TINV * PMAX * PMAX, p);
     load_mat<PP>(mAX, a.mats + M_ALPHAXI * PMAX * PMAX, p);
@@ -1008,27 +1021,35 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
   Fac<PP, S> BE{G::MATS_SMEM ? mB : reinterpret_cast<const C*>(a.mats + M_BETA * PMAX * PMAX), p};
   GramAcc<G::NTRI, S, M3G> g;
   g.init(G_SYM, p, lane);
-  if constexpr (OT) {
+  if constexpr (OT || OTZ) {
     // one tile per warp (p = 32): the same updates, S_m and U_m streamed from global memory
+    // (FP64 three-product applies, or the tensor-core applies splitting them from there)
     for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
       const int64_t r0 = c * CHUNK;
       const int rows = (int)min((int64_t)CHUNK, n - r0);
       load_tile<PP>(b0, a.W, r0, n, p, lane);
       __syncwarp();
-      tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);   // Q_{m+1}
+      if constexpr (OTZ) oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane);
+      else tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);   // Q_{m+1}
       __syncwarp();
       store_tile<PP>(a.Q, b0, r0, n, p, lane);
       if (!first) {
         __syncwarp();
         load_tile<PP>(b0, a.X, r0, n, p, lane);
         __syncwarp();
-        apply_full3_g<PP, false>(b0, b0, a.S + r0 * p, rows, Fac3(a.mats, M_ALPHAXI, p), p, lane);   // X_{m+1}
+        if constexpr (OTZ)
+          oz_apply_gin<PP, false, true>(b0, b0, a.S + r0 * p, rows, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane);
+        else
+          apply_full3_g<PP, false>(b0, b0, a.S + r0 * p, rows, Fac3(a.mats, M_ALPHAXI, p), p, lane);   // X_{m+1}
         __syncwarp();
         store_tile<PP>(a.X, b0, r0, n, p, lane);
         __syncwarp();
         load_tile<PP>(b0, a.Q, r0, n, p, lane);   // Q_{m+1}, just stored
         __syncwarp();
-        apply_full3_g<PP, false>(b0, b0, a.S + r0 * p, rows, Fac3(a.mats, M_BETA, p), p, lane);   // S_{m+1}
+        if constexpr (OTZ)
+          oz_apply_gin<PP, false, true>(b0, b0, a.S + r0 * p, rows, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane);
+        else
+          apply_full3_g<PP, false>(b0, b0, a.S + r0 * p, rows, Fac3(a.mats, M_BETA, p), p, lane);   // S_{m+1}
       }
       __syncwarp();
       store_tile<PP>(a.S, b0, r0, n, p, lane);       // (setup: S_0 = Q_0)
@@ -1037,7 +1058,10 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       load_tile<PP>(b0, a.V, r0, n, p, lane);
       __syncwarp();
       if (!first) {
-        apply_full3_g<PP, false>(b0, b0, a.U + r0 * p, rows, Fac3(a.mats, M_BETA, p), p, lane);   // U_{m+1}
+        if constexpr (OTZ)
+          oz_apply_gin<PP, false, true>(b0, b0, a.U + r0 * p, rows, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane);
+        else
+          apply_full3_g<PP, false>(b0, b0, a.U + r0 * p, rows, Fac3(a.mats, M_BETA, p), p, lane);   // U_{m+1}
         __syncwarp();
       }
       g.template add<false>(b0, b0, lane);
@@ -1054,7 +1078,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
     load_tile<PP>(b0, blk<C>(a.W), r0, n, p, lane);
     __syncwarp();
     if constexpr (OZ) {
-      oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane, adig);
+      oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane);
     } else if constexpr (M3A) {
       tri_apply3_inplace<PP>(b0, Fac3(a.mats, M_TINV, p), p, lane);       // Q_{m+1}
     } else if constexpr (G::MATS_SMEM) {
@@ -1071,7 +1095,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       load_tile<PP>(b1, blk<C>(a.S), r0, n, p, lane);
       __syncwarp();
       if constexpr (OZ) {
-        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane, adig);
+        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane);
       } else if constexpr (M3A) {
         apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_ALPHAXI, p), p, lane);   // X_{m+1}
       } else {
@@ -1083,7 +1107,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
       load_tile<PP>(b0, blk<C>(a.Q), r0, n, p, lane);      // Q_{m+1}, just stored
       __syncwarp();
       if constexpr (OZ) {
-        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane, adig);
+        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane);
       } else if constexpr (M3A) {
         apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);      // S_{m+1} = Q + S beta'
       } else {
@@ -1099,7 +1123,7 @@ __device__ __forceinline__ void d_cocr_passC(const PassArgs& a, const int vblk, 
     __syncwarp();
     if (!first) {
       if constexpr (OZ) {
-        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane, adig);
+        oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane);
       } else if constexpr (M3A) {
         apply_full3<PP, false>(b0, b0, b1, Fac3(a.mats, M_BETA, p), p, lane);      // U_{m+1} = V + U beta'
       } else {
@@ -1128,10 +1152,10 @@ __global__ void __launch_bounds__(NWARP * 32, one_tile<PP, S, OZ>() ? 2 : 3) k_c
   d_cocr_passC<PP, S, OZ>(a, blockIdx.x, gridDim.x);
 }
 // The tensor-core pass C: up to p = 16 its shared memory allows 3 CTAs per SM, and so does
-// this bound on its registers (otherwise about 238, 2 per SM); at p = 32 shared memory
-// allows one.
+// this bound on its registers (otherwise about 238, 2 per SM); at p = 32 (one tile per
+// warp) two.
 template <int PP>
-__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 1 : 3) k_cocr_passC_tc(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? 2 : 3) k_cocr_passC_tc(const PassArgs a) {
   d_cocr_passC<PP, double, true>(a, blockIdx.x, gridDim.x);
 }
 
@@ -1213,7 +1237,6 @@ __device__ __forceinline__ void d_cocg_pass1_tc(const PassArgs& a, const int vbl
   C* tiles = smem;   // no staged factors: the applies read slice fragments
   C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
-  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, true>();
   GramAcc<G::NTRI, double, M3G> gh, gs;
   gh.init(G_HERM, p, lane);
   gs.init(G_SYM, p, lane);
@@ -1222,7 +1245,7 @@ __device__ __forceinline__ void d_cocg_pass1_tc(const PassArgs& a, const int vbl
     load_tile<PP>(b0, a.Q, r0, n, p, lane);
     load_tile<PP>(b1, a.V, r0, n, p, lane);
     __syncwarp();
-    oz_apply_any<PP, true, true>(b0, b0, b1, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane, adig);   // W = Q - A S alpha'
+    oz_apply_any<PP, true, true>(b0, b0, b1, a.oz + OZ_ALPHA * OZ_SLOT_U2, p, lane);   // W = Q - A S alpha'
     __syncwarp();
     if constexpr (M3G) {
       sd_tile<PP>(b1, b0, p, lane);   // A S_m is no longer needed
@@ -1238,7 +1261,7 @@ __device__ __forceinline__ void d_cocg_pass1_tc(const PassArgs& a, const int vbl
     load_tile<PP>(b0, a.X, r0, n, p, lane);
     load_tile<PP>(b1, a.S, r0, n, p, lane);
     __syncwarp();
-    oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane, adig);   // X_{m+1}
+    oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_ALPHAXI * OZ_SLOT_U2, p, lane);   // X_{m+1}
     __syncwarp();
     store_tile<PP>(a.X, b0, r0, n, p, lane);
     __syncwarp();
@@ -1264,18 +1287,17 @@ __device__ __forceinline__ void d_cocg_pass2_tc(const PassArgs& a, const int vbl
   C* tiles = smem;
   C* b0 = tiles + warp * 2 * G::TILE;
   C* b1 = b0 + G::TILE;
-  uint4* adig = reinterpret_cast<uint4*>(tiles + NWARP * 2 * G::TILE) + warp * oz_adig_u4<PP, true>();
   for (int64_t c = (int64_t)vblk * NWARP + warp; c < nchunks; c += cstride) {
     const int64_t r0 = c * CHUNK;
     load_tile<PP>(b0, a.W, r0, n, p, lane);
     if (!first) load_tile<PP>(b1, a.S, r0, n, p, lane);
     __syncwarp();
-    oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane, adig);   // Q_{m+1}
+    oz_apply_any<PP, false, false>(b0, nullptr, b0, a.oz + OZ_T * OZ_SLOT_U2, p, lane);   // Q_{m+1}
     __syncwarp();
     store_tile<PP>(a.Q, b0, r0, n, p, lane);
     if (!first) {
       __syncwarp();
-      oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane, adig);   // S_{m+1}
+      oz_apply_any<PP, false, true>(b0, b0, b1, a.oz + OZ_BETA * OZ_SLOT_U2, p, lane);   // S_{m+1}
     }
     __syncwarp();
     store_tile<PP>(a.S, b0, r0, n, p, lane);
@@ -1424,7 +1446,8 @@ constexpr size_t pass_smem(int kind) {
                               kind == K_COCG_2);
   const bool oz_cocg = OZ && (kind == K_COCG_1 || kind == K_COCG_2);
   const bool m3 = (m3_apply<PP, S>() && !oz_kind) || oz_cocg;   // oz_cocg: no staged factors either
-  const bool ot = one_tile<PP, S, OZ>() && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C);
+  const bool ot = (one_tile<PP, S, OZ>() && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C)) ||
+                  (tc_one_tile<PP, OZ>() && (kind == K_COCR_A || kind == K_COCR_C));
   const int nt = (kind == K_QR2 && qr2_m3<PP, S>()) ? 2 : ((oz_cocg ? 2 : ntiles[kind]) / (ot ? 2 : 1));
   const size_t mats =
       m3 ? 0 : (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
@@ -1437,7 +1460,6 @@ constexpr size_t pass_smem(int kind) {
   if (has_gram && s < mats + red) s = mats + red;
   if (oz_gram<PP, OZ>() && (kind == K_COCR_A || kind == K_SPMM_GRAM))
     s += (size_t)NWARP * OzGramGeo<PP>::ACC * sizeof(double);
-  if (oz_kind) s += (size_t)NWARP * oz_adig_u4<PP, OZ>() * sizeof(uint4);   // p = 32: staged A digits
   return s;
 }
 
