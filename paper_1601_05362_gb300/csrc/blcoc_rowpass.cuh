@@ -262,12 +262,9 @@ constexpr bool one_tile() { return PP >= 32 && sizeof(S) == 8 && !OZ; }
 // of 64 x 64 real entries per warp would not fit beside the tiles).
 template <int PP, bool OZ>
 constexpr bool oz_gram() { return OZ && PP <= 16; }
-// The tensor-core kernel set's SpMM: the tensor-core variant (T apply, W^T Y Gram on the
-// tensor cores) up to p = 16; at p = 32 the FP64 one-tile SpMM, which is faster there
-// (17.7 against 22.5 ms on the 128^3 problem) because only its triangular T apply would
-// run on the tensor cores.
-template <int PP>
-constexpr bool oz_spmm() { return PP <= 16; }
+// The tensor-core kernel set's SpMM has the T apply on the tensor cores, and up to p = 16
+// the W^T Y Gram as well; at p = 32 it keeps one tile per warp (W for its FP64 Gram read
+// from global memory), as the FP64 SpMM there does.
 
 // The tensor-core passes A and C at p = 32 keep one tile per warp, as the FP64 ones do:
 // the second operand of each block update is split into slice digits straight from global
@@ -832,13 +829,14 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
-  constexpr bool OT = one_tile<PP, S, OZ>();   // W for the Gram read from global memory
+  // W for the Gram read from global memory (FP64 and tensor-core variants at p = 32)
+  constexpr bool OT = one_tile<PP, S, OZ>() || tc_one_tile<PP, OZ>();
   C* T_s = smem;
-  C* tiles = smem + (M3A ? 0 : mats_off<PP, S>(1));
+  C* tiles = smem + ((M3A || OZ) ? 0 : mats_off<PP, S>(1));   // the tensor-core apply reads slices
   C* tY = tiles + warp * (OT ? 1 : 2) * G::TILE;
   C* tW = tY + G::TILE;
   const bool applyT = a.flag & 1;
-  if constexpr (G::MATS_SMEM && !M3A) {
+  if constexpr (G::MATS_SMEM && !M3A && !OZ) {
     load_mat<PP>(T_s, a.mats + M_TINV * PMAX * PMAX, p);
     __syncthreads();
   }
@@ -886,7 +884,8 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
 // Two tiles per warp allow at most 3 CTAs per SM (1 at PP = 32), so registers up to that
 // bound cost no occupancy.
 template <int PP, typename S, bool OZ = false, int SPL = 1>
-__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? (one_tile<PP, S, OZ>() ? 2 : 1) : 3) k_spmm_gram(const PassArgs a) {
+__global__ void __launch_bounds__(NWARP * 32, PP >= 32 ? ((one_tile<PP, S, OZ>() || tc_one_tile<PP, OZ>()) ? 2 : 1) : 3)
+    k_spmm_gram(const PassArgs a) {
   d_spmm_gram<PP, S, OZ, SPL>(a, blockIdx.x, gridDim.x);
 }
 
@@ -1445,9 +1444,11 @@ constexpr size_t pass_smem(int kind) {
   const bool oz_kind = OZ && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C || kind == K_COCG_1 ||
                               kind == K_COCG_2);
   const bool oz_cocg = OZ && (kind == K_COCG_1 || kind == K_COCG_2);
-  const bool m3 = (m3_apply<PP, S>() && !oz_kind) || oz_cocg;   // oz_cocg: no staged factors either
-  const bool ot = (one_tile<PP, S, OZ>() && (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C)) ||
-                  (tc_one_tile<PP, OZ>() && (kind == K_COCR_A || kind == K_COCR_C));
+  // no staged factors: three-product applies, the bl_cocg_rq tensor-core passes and the
+  // tensor-core SpMM (their applies read slice fragments)
+  const bool m3 = (m3_apply<PP, S>() && !oz_kind) || oz_cocg || (OZ && kind == K_SPMM_GRAM);
+  const bool ot = (one_tile<PP, S, OZ>() || tc_one_tile<PP, OZ>()) &&
+                  (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C);
   const int nt = (kind == K_QR2 && qr2_m3<PP, S>()) ? 2 : ((oz_cocg ? 2 : ntiles[kind]) / (ot ? 2 : 1));
   const size_t mats =
       m3 ? 0 : (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
@@ -1588,8 +1589,8 @@ void prepare_pass_kernels_tc() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || done[dev]) return;
-  cudaFuncSetAttribute(k_spmm_gram<PP, double, oz_spmm<PP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pass_smem<PP, double, oz_spmm<PP>()>(K_SPMM_GRAM));
+  cudaFuncSetAttribute(k_spmm_gram<PP, double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pass_smem<PP, double, true>(K_SPMM_GRAM));
   cudaFuncSetAttribute(k_cocr_passA_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCR_A));
   cudaFuncSetAttribute(k_cocr_passC_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1598,15 +1599,14 @@ void prepare_pass_kernels_tc() {
                        (int)pass_smem<PP, double, true>(K_COCG_1));
   cudaFuncSetAttribute(k_cocg_pass2_tc<PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)pass_smem<PP, double, true>(K_COCG_2));
-  set_spmm_split_smem<PP, double, oz_spmm<PP>(), 2>();
-  set_spmm_split_smem<PP, double, oz_spmm<PP>(), 4>();
+  set_spmm_split_smem<PP, double, true, 2>();
+  set_spmm_split_smem<PP, double, true, 4>();
   done[dev] = true;
 }
 
-// Launch-grid rule of the tensor-core set: the SpMM's from its own kernel (see oz_spmm).
+// Launch-grid rule of the tensor-core set.
 template <int PP>
 int pass_grid_tc(int64_t n, int kind, int num_sms) {
-  if (kind == K_SPMM_GRAM && !oz_spmm<PP>()) return pass_grid<PP, double, false>(n, kind, num_sms);
   return pass_grid<PP, double, true>(n, kind, num_sms);
 }
 
@@ -1614,7 +1614,7 @@ template <int PP>
 const KernelSet& kernel_set_tc() {
   static const KernelSet ks = {
       &launch_pass<PP, double, K_RESID, k_resid<PP, double>>,
-      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, oz_spmm<PP>()>, oz_spmm<PP>()>,
+      &launch_pass<PP, double, K_SPMM_GRAM, k_spmm_gram<PP, double, true>, true>,
       &launch_pass<PP, double, K_SPMM_PLAIN, k_spmm_plain<PP, double>>,
       &launch_pass<PP, double, K_COCR_A, k_cocr_passA_tc<PP>, true>,
       &launch_pass<PP, double, K_COCR_C, k_cocr_passC_tc<PP>, true>,
@@ -1622,8 +1622,8 @@ const KernelSet& kernel_set_tc() {
       &launch_pass<PP, double, K_COCG_2, k_cocg_pass2_tc<PP>, true>,
       &launch_pass<PP, double, K_AXPY, k_axpy<PP, double>>,
       &launch_pass<PP, double, K_QR2, k_qr2<PP, double>>,
-      spmm_split_fn<PP, double, oz_spmm<PP>(), 2>(),
-      spmm_split_fn<PP, double, oz_spmm<PP>(), 4>(),
+      spmm_split_fn<PP, double, true, 2>(),
+      spmm_split_fn<PP, double, true, 4>(),
       &pass_grid_tc<PP>,
       &prepare_pass_kernels_tc<PP>,
   };
