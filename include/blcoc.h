@@ -246,9 +246,12 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  Yanagisawa): Cholesky of W^H W + s I with s = 11 (n p + p(p+1)) u
  *                  trace(W^H W), then two Cholesky QR passes; a breakdown is reported
  *                  only if the resulting factor has a diagonal entry below 1e-14 of its
- *                  largest (the rank test of a Householder QR).  The six kernels of the
- *                  fallback are in every iteration and return at once unless it is
- *                  needed.  0: a failed Cholesky QR is a breakdown.
+ *                  largest (the rank test of a Householder QR).  In the CUDA graph of
+ *                  the iterations the fallback's six kernels form the body of a
+ *                  conditional node that the Cholesky stage enables only when it is
+ *                  needed; launched directly (option graph = 0) they run in every
+ *                  iteration and return at once unless it is needed.  0: a failed
+ *                  Cholesky QR is a breakdown.
  *   "spmm_split" : the SpMM's row bundle.  1 (default): p lanes per row (one per column),
  *                  each summing the row's nonzeros in order.  2 or 4: that many lane groups
  *                  split each row's nonzeros (interleaved) and their partial sums are
@@ -275,7 +278,8 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value);
 /* blcoc_get_stat - counters of the last solve: "launches" (kernels launched by the
  * solve, including those inside graph replays), "graph_replays", "outer_iters",
  * "persistent_graph" (last persistent batch: 1 graph replays, 0 direct launches, -1 none),
- * "spmm_split" (SpMM row bundle of the last solve)
+ * "spmm_split" (SpMM row bundle of the last solve), "qr_fallbacks" (shifted-CholQR3
+ * fallbacks started in the last solve)
  * (refinement steps of a mixed solve), and with the
  * "timing" option "kt_ns.<kernel>" (total device nanoseconds) and "kt_n.<kernel>"
  * (launches that did work) for <kernel> in resid, spmm_gram, spmm_plain, cocr_passA,

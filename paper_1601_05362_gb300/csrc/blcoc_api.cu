@@ -163,6 +163,10 @@ struct blcoc_ctx {
   int qr_passes = 1;          // 2: CholQR2 (one re-orthogonalising pass after every Cholesky QR)
   int qr_fallback = 1;        // rq methods, qr_passes = 1: shifted-CholQR3 fallback when a Cholesky QR fails
   int spmm_split = 1;         // SpMM row bundle (1, 2, 4); 0: timed sweep, cached per (n, nnz/row, p)
+  // captured iterations hold the QR fallback's launches in a conditional graph node (0 after
+  // the runtime refused one: they are then captured as plain launches that return at once)
+  int cond_ok = 1;
+  cudaStream_t sbody = nullptr;   // captures the conditional node's body
   int stat_spmm_split = 0;    // row bundle of the last solve
   int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
   int persistent_stall = 0;   // persistent batch, test hook: no first work item is published
@@ -380,7 +384,8 @@ struct Solver {
   void small(SmallKind k, int ne) {
     Timer t;
     if (time_small) timed_begin(t, kKindSmall0 + (int)k);
-    launch_small(k, p, method + 16 * plain + 32 * qr2, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s, oz);
+    launch_small(k, p, method + 16 * plain + 32 * qr2, h->stage1, ne, h->mats, h->ctrl, h->hist, h->s, oz,
+                 k == SK_CHOL ? cond : 0ull);
     if (time_small) timed_end(t);
     ++launches;
   }
@@ -406,14 +411,89 @@ struct Solver {
   // stage before had to shift the Gram, two Cholesky QR passes complete the factorisation;
   // otherwise these kernels return at once.
   int qr_fb = 0;
-  void fallback_qr(bool setup) {
-    if (!qr_fb) return;
+  void fallback_launches(bool setup) {
     const int E = tri_count(p), ne = method == BLCOC_COCG_RQ ? 2 * E : E;
     for (int k = 0; k < 2; ++k) {
       pass(K->qr2, K_QR2, ne, F_FB | (method == BLCOC_COCG_RQ ? F_SYM2 : 0), nullptr, kKindQR2);
       reduce(ne, h->ctrl, true);
       small(setup ? SK_CHOL_FB_SETUP : SK_CHOL_FB, ne);
     }
+  }
+  // Shifted-CholQR3 fallback after a Cholesky QR.  Launched directly, its kernels return at
+  // once unless the preceding stage started it.  In a captured iteration they form the body
+  // of a conditional IF node whose handle that stage (SK_CHOL) sets, so a replay that needs
+  // no fallback runs none of them.
+  void fallback_qr(bool setup) {
+    if (!qr_fb) return;
+    if (!setup && cond != 0) {
+      const bool ok = fallback_conditional();
+      cond = 0;
+      if (ok) return;
+      cond_failed = true;   // the caller discards this capture and captures plain launches
+    }
+    fallback_launches(setup);
+  }
+  // conditional graph node of the current iteration's fallback (captured graphs)
+  unsigned long long cond = 0;
+  bool cond_failed = false;
+  void cond_begin() {
+    cond = 0;
+    if (!capturing || !qr_fb || !h->cond_ok || cond_failed) return;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t cg = nullptr;
+    cudaGraphConditionalHandle hd = 0;
+    if (cudaStreamGetCaptureInfo(h->s, &st, nullptr, &cg) != cudaSuccess || st != cudaStreamCaptureStatusActive ||
+        cudaGraphConditionalHandleCreate(&hd, cg, 0, cudaGraphCondAssignDefault) != cudaSuccess) {
+      cudaGetLastError();
+      cond_failed = true;
+      return;
+    }
+    cond = (unsigned long long)hd;
+  }
+  bool fallback_conditional() {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(h->s, &st, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
+        st != cudaStreamCaptureStatusActive)
+      return cudaGetLastError(), false;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = (cudaGraphConditionalHandle)cond;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np) != cudaSuccess ||
+        cudaStreamUpdateCaptureDependencies(h->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+      return cudaGetLastError(), false;
+    if (!h->sbody && cudaStreamCreateWithFlags(&h->sbody, cudaStreamNonBlocking) != cudaSuccess)
+      return cudaGetLastError(), false;
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(h->sbody, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      return cudaGetLastError(), false;
+    // the body's launches: on the body stream, untimed (event nodes are not allowed in a
+    // conditional body) and not counted (they run only when needed)
+    cudaStream_t main_s = h->s;
+    std::vector<Timer>* keep_timers = timers;
+    const bool keep_small = time_small;
+    const int keep_launches = launches;
+    h->s = h->sbody;
+    timers = nullptr;
+    time_small = false;
+    fallback_launches(false);
+    h->s = main_s;
+    timers = keep_timers;
+    time_small = keep_small;
+    launches = keep_launches;
+    cudaGraph_t out = nullptr;
+    if (cudaStreamEndCapture(h->sbody, &out) != cudaSuccess) return cudaGetLastError(), false;
+    return true;
+  }
+  void chol_stage(int ne) {
+    cond_begin();
+    small(SK_CHOL, ne);
   }
 
   // inner = 1: the right-hand side of this solve is the residual itself (refinement
@@ -447,7 +527,7 @@ struct Solver {
       small(SK_ALPHA, E);
       pass(K->cocr_passA, K_COCR_A, E, 0);
       reduce(E, h->ctrl);
-      small(SK_CHOL, E);
+      chol_stage(E);
       second_qr(false);
       fallback_qr(false);
       pass(spmm_fn(), K_SPMM_GRAM, E, 0);            // Y = A W, gram W^T Y (for H+ of the beta' step)
@@ -474,7 +554,7 @@ struct Solver {
       small(SK_ALPHA, E);
       pass(K->cocr_passA, K_COCR_A, E, 0);
       reduce(E, h->ctrl);
-      small(SK_CHOL, E);
+      chol_stage(E);
       second_qr(false);
       fallback_qr(false);
       pass(spmm_fn(), K_SPMM_GRAM, E, 1);
@@ -486,7 +566,7 @@ struct Solver {
       small(SK_ALPHA, E);
       pass(K->cocg_pass1, K_COCG_1, 2 * E, 0);
       reduce(2 * E, h->ctrl);
-      small(SK_CHOL, 2 * E);
+      chol_stage(2 * E);
       second_qr(false);
       fallback_qr(false);
       pass(K->cocg_pass2, K_COCG_2, 0, 0);
@@ -570,6 +650,7 @@ blcoc_status blcoc_destroy(blcoc_handle h) {
   for (cudaEvent_t e : h->evpool) cudaEventDestroy(e);
   if (h->ev) cudaEventDestroy(h->ev);
   if (h->s) cudaStreamDestroy(h->s);
+  if (h->sbody) cudaStreamDestroy(h->sbody);
   delete h;
   cudaSetDevice(cur);
   return BLCOC_OK;
@@ -765,6 +846,7 @@ blcoc_status blcoc_get_stat(blcoc_handle h, const char* key, int64_t* value) {
   if (!strcmp(key, "outer_iters")) { *value = h->outer_iters; return BLCOC_OK; }
   if (!strcmp(key, "persistent_graph")) { *value = h->stat_persistent_graph; return BLCOC_OK; }
   if (!strcmp(key, "spmm_split")) { *value = h->stat_spmm_split; return BLCOC_OK; }
+  if (!strcmp(key, "qr_fallbacks")) { *value = h->h_ctrl ? h->h_ctrl->fb_count : 0; return BLCOC_OK; }
   for (int k = 0; k < kNumKinds; ++k) {
     const std::string nm(kKindNames[k]);
     if (("kt_ns." + nm) == key) { *value = (int64_t)(h->kt_ms[k] * 1e6); return BLCOC_OK; }
@@ -835,22 +917,36 @@ blcoc_status run_iterations(blcoc_ctx* h, Solver& sv, const GraphKey& gkey, int 
       g.reset();
       h->evnext = 0;
       cudaGraph_t graph = nullptr;
-      CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
-      const int before = sv.launches;
-      sv.timers = h->timing ? &g.timers : nullptr;
-      sv.set_timing_mode(h->timing);
-      sv.capturing = true;
-      for (int i = 0; i < batch; ++i) {
-        sv.batch_iter = i;
-        sv.iteration();
+      for (;;) {   // a second capture with plain launches if a conditional node was refused
+        CK(h, cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+        const int before = sv.launches;
+        g.timers.clear();
+        h->evnext = 0;
+        sv.timers = h->timing ? &g.timers : nullptr;
+        sv.set_timing_mode(h->timing);
+        sv.capturing = true;
+        for (int i = 0; i < batch; ++i) {
+          sv.batch_iter = i;
+          sv.iteration();
+        }
+        sv.capturing = false;
+        sv.timers = nullptr;
+        g.timing = h->timing;
+        g.launches = sv.launches - before;
+        sv.launches = before;
+        cudaError_t e = cudaStreamEndCapture(h->s, &graph);
+        if (sv.cond_failed) {
+          if (graph) cudaGraphDestroy(graph);
+          graph = nullptr;
+          cudaGetLastError();
+          h->cond_ok = 0;
+          sv.cond_failed = false;
+          continue;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        break;
       }
-      sv.capturing = false;
-      sv.timers = nullptr;
-      g.timing = h->timing;
-      g.launches = sv.launches - before;
-      sv.launches = before;
-      cudaError_t e = cudaStreamEndCapture(h->s, &graph);
-      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      cudaError_t e = cudaSuccess;
       e = cudaGraphInstantiate(&g.exec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) {
@@ -1522,22 +1618,41 @@ static blcoc_status solve_batched_impl(int form, int nsys, const blcoc_handle* h
     // one graph: every live system's `poll` iterations as a parallel branch
     auto capture = [&](int poll, int grid_sms, cudaGraphExec_t* exec, int* nlaunch) -> blcoc_status {
       cudaGraph_t graph = nullptr;
-      CK(h0, cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
-      CK(h0, cudaEventRecord(fork_ev, main_s));
       int launches = 0;
-      for (int i = 0; i < nsys; ++i) {
-        if (!live[i]) continue;
-        CK(h0, cudaStreamWaitEvent(hs[i]->s, fork_ev, 0));
-        sv[i].grid_sms = grid_sms;
-        const int before = sv[i].launches;
-        for (int k = 0; k < poll; ++k) sv[i].iteration();
-        launches += sv[i].launches - before;
-        sv[i].launches = before;
-        CK(h0, cudaEventRecord(join[i], hs[i]->s));
-        CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
+      for (;;) {   // a second capture with plain launches if a conditional node was refused
+        CK(h0, cudaStreamBeginCapture(main_s, cudaStreamCaptureModeThreadLocal));
+        CK(h0, cudaEventRecord(fork_ev, main_s));
+        launches = 0;
+        bool refused = false;
+        for (int i = 0; i < nsys; ++i) {
+          if (!live[i]) continue;
+          CK(h0, cudaStreamWaitEvent(hs[i]->s, fork_ev, 0));
+          sv[i].grid_sms = grid_sms;
+          sv[i].capturing = true;
+          const int before = sv[i].launches;
+          for (int k = 0; k < poll; ++k) sv[i].iteration();
+          sv[i].capturing = false;
+          launches += sv[i].launches - before;
+          sv[i].launches = before;
+          refused = refused || sv[i].cond_failed;
+          CK(h0, cudaEventRecord(join[i], hs[i]->s));
+          CK(h0, cudaStreamWaitEvent(main_s, join[i], 0));
+        }
+        cudaError_t e = cudaStreamEndCapture(main_s, &graph);
+        if (refused) {
+          if (graph) cudaGraphDestroy(graph);
+          graph = nullptr;
+          cudaGetLastError();
+          for (int i = 0; i < nsys; ++i) {
+            hs[i]->cond_ok = 0;
+            sv[i].cond_failed = false;
+          }
+          continue;
+        }
+        if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaStreamEndCapture");
+        break;
       }
-      cudaError_t e = cudaStreamEndCapture(main_s, &graph);
-      if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaStreamEndCapture");
+      cudaError_t e = cudaSuccess;
       e = cudaGraphInstantiate(exec, graph, 0);
       cudaGraphDestroy(graph);
       if (e != cudaSuccess) return cuda_fail(h0, e, "batched: cudaGraphInstantiate");

@@ -42,6 +42,7 @@ struct Ctrl {
   double sumsq_b; // sum |B_ij|^2 (setup)
   double pad[2];
   double qr_shift; // fallback shift coefficient 11 (n p + p (p + 1)) u (times trace(W^H W))
+  int fb_count;    // shifted-CholQR3 fallbacks started in this solve
 };
 
 // PassArgs::flag bit shared with the host: the row pass runs only while a shifted-CholQR3

@@ -49,10 +49,14 @@ __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* m
   else d_small_alpha(S, p, stage1, ncomp, mats, ctrl, hist, plain, oz);
 }
 
+// cond != 0: the handle of the conditional graph node that holds this iteration's
+// shifted-CholQR3 fallback passes; set to run them only when the fallback has started.
 __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
-                             int plain, uint2* oz, int qr2) {
+                             int plain, uint2* oz, int qr2, unsigned long long cond) {
   SMALL_PROLOGUE
   d_small_chol(S, p, method, stage1, ncomp, mats, ctrl, plain, oz, qr2);
+  if (cond != 0 && threadIdx.x == 0)
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, BLCOC_LD(&ctrl->qr_fb) != 0 ? 1u : 0u);
 }
 
 __global__ void k_small_chol2(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
@@ -161,7 +165,7 @@ void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, 
 }
 
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
-                  double* hist, cudaStream_t s, uint2* oz) {
+                  double* hist, cudaStream_t s, uint2* oz, unsigned long long cond) {
   const size_t sm = small_smem();
   const int ncomp = 2 * ne;
   // method: 0 cocg / 1 cocr, +16 plain form, +32 CholQR2
@@ -181,7 +185,7 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
     case SK_ALPHA:
       k_small_alpha<<<m == 1 ? 2 : 1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz);
       break;
-    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2); break;
+    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2, cond); break;
     case SK_COCR_BETA:   // a CTA per column; one CTA where the exact-slice form is emitted
       k_small_cocr_beta<<<oz != nullptr ? 1 : p, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, oz);
       break;

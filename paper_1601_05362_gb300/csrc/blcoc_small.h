@@ -14,9 +14,10 @@ void launch_reduce(const double2* partials, int nparts, int ne, double* stage1, 
                    bool fb_only = false);
 // method: 0 cocg / 1 cocr, + 16 for the plain forms, + 32 for CholQR2.
 // oz != nullptr: also write the exact-slice fragments of the factors formed (tensor-core
-// applies of the FP64 path, p <= 16).
+// applies of the FP64 path).  cond (SK_CHOL only, inside a captured graph): the conditional
+// node handle the stage sets to 1 when a shifted-CholQR3 fallback has started, 0 otherwise.
 void launch_small(SmallKind kind, int p, int method, const double* stage1, int ne, double2* mats, Ctrl* ctrl,
-                  double* hist, cudaStream_t s, uint2* oz = nullptr);
+                  double* hist, cudaStream_t s, uint2* oz = nullptr, unsigned long long cond = 0);
 void launch_sampled_grad(int64_t n, const int* rp, const int* ci, const double2* Lam, const double2* X, int p,
                          double2* out, int num_sms, cudaStream_t s);
 void launch_validate(int64_t n, int64_t nnz, const int* rp, const int* ci, const double2* va, int* flags, int which,

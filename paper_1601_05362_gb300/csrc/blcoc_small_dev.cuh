@@ -425,7 +425,10 @@ __device__ int chol_gram(SmallShared& S, int p, Ctrl* ctrl) {
   for (int j = threadIdx.x; j < p; j += blockDim.x) S.m[0][j * LD + j].x += sh;
   __syncthreads();
   if (!chol_upper(S.m[0], S.m[1], p, S.red)) return 0;
-  if (threadIdx.x == 0) ctrl->qr_fb = 2;
+  if (threadIdx.x == 0) {
+    ctrl->qr_fb = 2;
+    ctrl->fb_count += 1;
+  }
   __syncthreads();
   return 2;
 }

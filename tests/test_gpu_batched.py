@@ -184,3 +184,31 @@ def test_batched_graph_runs_the_qr_fallback_like_separate_solves():
     for (Xg, ig), (Xs_, is_) in zip(graph, sep):
         assert ig["iters"] == is_["iters"]
         assert np.array_equal(Xg, Xs_) and np.array_equal(ig["hist"], is_["hist"])
+
+
+@pytest.mark.parametrize("method", ["cocr_rq", "cocg_rq"])
+def test_fallback_inside_the_graph_matches_direct_launches(method):
+    """In the iterations' CUDA graph the shifted-CholQR3 fallback is a conditional node that
+    the Cholesky stage enables only when needed; launched directly its kernels run every
+    iteration and return at once.  Both give the same bits, iteration count and number of
+    fallbacks, and (bl_cocr_rq) at least one of these tiny systems does fall back."""
+    torch = need_gpu()
+    from paper_1601_05362_gb300 import blcoc
+    tiny = P.helmholtz2d_batch(40, seed=11, side_range=(6, 14), k_range=(2.0, 5.0))
+    fell = 0
+    for pr in tiny:
+        out = []
+        for graph in (1, 0):
+            h = blcoc.Handle.from_csr(pr.A)
+            h.set_option("graph", graph)
+            B = to_dev(torch, pr.B)
+            X = torch.zeros_like(B)
+            st = h.solve(B, X, method=method, tol=1e-10, maxit=30, check=False)
+            out.append((st, X.cpu().numpy(), h.info()["iters"], h.stat("qr_fallbacks")))
+            h.close()
+        (s1, X1, i1, f1), (s0, X0, i0, f0) = out
+        assert (s1, i1, f1) == (s0, i0, f0)
+        assert np.array_equal(X1, X0)
+        fell += f1 > 0
+    if method == "cocr_rq":
+        assert fell >= 1
