@@ -246,12 +246,18 @@ blcoc_status blcoc_sampled_grad(blcoc_handle h, const void* Lambda, const void* 
  *                  Yanagisawa): Cholesky of W^H W + s I with s = 11 (n p + p(p+1)) u
  *                  trace(W^H W), then two Cholesky QR passes; a breakdown is reported
  *                  only if the resulting factor has a diagonal entry below 1e-14 of its
- *                  largest (the rank test of a Householder QR).  In the CUDA graph of
- *                  the iterations the fallback's six kernels form the body of a
- *                  conditional node that the Cholesky stage enables only when it is
- *                  needed; launched directly (option graph = 0) they run in every
- *                  iteration and return at once unless it is needed.  0: a failed
- *                  Cholesky QR is a breakdown.
+ *                  largest (the rank test of a Householder QR).  The fallback's six
+ *                  kernels run in every iteration and return at once unless it is
+ *                  needed (see "graph_conditional").  0: a failed Cholesky QR is a
+ *                  breakdown.
+ *   "graph_conditional": 1 - in the CUDA graph of the iterations the QR fallback's six
+ *                  kernels form the body of a conditional node that the Cholesky stage
+ *                  enables only when a fallback has started, so an iteration that needs
+ *                  none launches none of them (same results bit for bit).  0 (default):
+ *                  plain launches; Nsight Compute does not profile the kernel nodes of a
+ *                  graph that can hold conditional nodes.  If the runtime refuses the
+ *                  conditional node the option turns itself off.  Also read per handle by
+ *                  blcoc_solve_batched.
  *   "spmm_split" : the SpMM's row bundle.  1 (default): p lanes per row (one per column),
  *                  each summing the row's nonzeros in order.  2 or 4: that many lane groups
  *                  split each row's nonzeros (interleaved) and their partial sums are

@@ -163,9 +163,11 @@ struct blcoc_ctx {
   int qr_passes = 1;          // 2: CholQR2 (one re-orthogonalising pass after every Cholesky QR)
   int qr_fallback = 1;        // rq methods, qr_passes = 1: shifted-CholQR3 fallback when a Cholesky QR fails
   int spmm_split = 1;         // SpMM row bundle (1, 2, 4); 0: timed sweep, cached per (n, nnz/row, p)
-  // captured iterations hold the QR fallback's launches in a conditional graph node (0 after
-  // the runtime refused one: they are then captured as plain launches that return at once)
-  int cond_ok = 1;
+  // option graph_conditional: captured iterations hold the QR fallback's launches in a
+  // conditional graph node (reset to 0 if the runtime refuses one: they are then captured
+  // as plain launches that return at once).  Off by default: Nsight Compute does not profile
+  // the kernel nodes of a graph that can hold conditional nodes.
+  int cond_ok = 0;
   cudaStream_t sbody = nullptr;   // captures the conditional node's body
   int stat_spmm_split = 0;    // row bundle of the last solve
   int persistent_timeout_ms = 10000;   // persistent batch: limit of one wait of the kernel
@@ -767,6 +769,12 @@ blcoc_status blcoc_set_option(blcoc_handle h, const char* key, int64_t value) {
   if (!strcmp(key, "graph")) {
     if (value != 0 && value != 1) return invalid(h, "graph must be 0 or 1");
     h->use_graph = (int)value;
+    return BLCOC_OK;
+  }
+  if (!strcmp(key, "graph_conditional")) {
+    if (value != 0 && value != 1) return invalid(h, "graph_conditional must be 0 or 1");
+    if (h->cond_ok != (int)value) h->graph.reset();
+    h->cond_ok = (int)value;
     return BLCOC_OK;
   }
   if (!strcmp(key, "timing")) {

@@ -49,14 +49,19 @@ __global__ void k_small_alpha(int p, const double* stage1, int ncomp, double2* m
   else d_small_alpha(S, p, stage1, ncomp, mats, ctrl, hist, plain, oz);
 }
 
-// cond != 0: the handle of the conditional graph node that holds this iteration's
-// shifted-CholQR3 fallback passes; set to run them only when the fallback has started.
+// COND: cond is the handle of the conditional graph node that holds this iteration's
+// shifted-CholQR3 fallback passes, set to run them only when the fallback has started.  A
+// separate instantiation, because Nsight Compute leaves out of its profile every kernel
+// that contains the device-side graph call, whether or not it runs.
+template <bool COND>
 __global__ void k_small_chol(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
                              int plain, uint2* oz, int qr2, unsigned long long cond) {
   SMALL_PROLOGUE
   d_small_chol(S, p, method, stage1, ncomp, mats, ctrl, plain, oz, qr2);
-  if (cond != 0 && threadIdx.x == 0)
-    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, BLCOC_LD(&ctrl->qr_fb) != 0 ? 1u : 0u);
+  if constexpr (COND) {
+    if (threadIdx.x == 0)
+      cudaGraphSetConditional((cudaGraphConditionalHandle)cond, BLCOC_LD(&ctrl->qr_fb) != 0 ? 1u : 0u);
+  }
 }
 
 __global__ void k_small_chol2(int p, int method, const double* stage1, int ncomp, double2* mats, Ctrl* ctrl,
@@ -146,7 +151,8 @@ static void set_small_attrs() {
   cudaFuncSetAttribute(k_small_setup, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_cocr_H0, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
-  cudaFuncSetAttribute(k_small_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_chol<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
+  cudaFuncSetAttribute(k_small_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_chol2, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_chol_fb, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
   cudaFuncSetAttribute(k_small_cocr_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, s);
@@ -185,7 +191,10 @@ void launch_small(SmallKind kind, int p, int method, const double* stage1, int n
     case SK_ALPHA:
       k_small_alpha<<<m == 1 ? 2 : 1, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, hist, plain, oz);
       break;
-    case SK_CHOL: k_small_chol<<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2, cond); break;
+    case SK_CHOL:
+      if (cond != 0) k_small_chol<true><<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2, cond);
+      else k_small_chol<false><<<1, SMALL_THREADS, sm, s>>>(p, m, stage1, ncomp, mats, ctrl, plain, oz, qr2, 0);
+      break;
     case SK_COCR_BETA:   // a CTA per column; one CTA where the exact-slice form is emitted
       k_small_cocr_beta<<<oz != nullptr ? 1 : p, SMALL_THREADS, sm, s>>>(p, stage1, ncomp, mats, ctrl, oz);
       break;

@@ -154,7 +154,8 @@ def test_batch_of_config_sized_systems_matches_oracle(persistent):
         h.close()
 
 
-def test_batched_graph_runs_the_qr_fallback_like_separate_solves():
+@pytest.mark.parametrize("conditional", [0, 1])
+def test_batched_graph_runs_the_qr_fallback_like_separate_solves(conditional):
     """Tiny systems near finite termination lose rank to the single-pass Cholesky QR's
     resolution (one of these 40 does at iteration 6); blcoc_solve then completes the QR as
     shifted CholQR3 and converges.  The graph form runs the same fallback per handle, so
@@ -165,6 +166,8 @@ def test_batched_graph_runs_the_qr_fallback_like_separate_solves():
 
     def run(batched):
         hs = [blcoc.Handle.from_csr(pr.A) for pr in tiny]
+        for h in hs:
+            h.set_option("graph_conditional", conditional)
         Bs = [to_dev(torch, pr.B) for pr in tiny]
         Xs = [torch.zeros_like(B) for B in Bs]
         if batched:
@@ -188,9 +191,9 @@ def test_batched_graph_runs_the_qr_fallback_like_separate_solves():
 
 @pytest.mark.parametrize("method", ["cocr_rq", "cocg_rq"])
 def test_fallback_inside_the_graph_matches_direct_launches(method):
-    """In the iterations' CUDA graph the shifted-CholQR3 fallback is a conditional node that
-    the Cholesky stage enables only when needed; launched directly its kernels run every
-    iteration and return at once.  Both give the same bits, iteration count and number of
+    """In the iterations' CUDA graph (option graph_conditional) the shifted-CholQR3 fallback
+    is a conditional node that the Cholesky stage enables only when needed; launched
+    directly its kernels run every iteration and return at once.  Both give the same bits, iteration count and number of
     fallbacks, and (bl_cocr_rq) at least one of these tiny systems does fall back."""
     torch = need_gpu()
     from paper_1601_05362_gb300 import blcoc
@@ -201,6 +204,7 @@ def test_fallback_inside_the_graph_matches_direct_launches(method):
         for graph in (1, 0):
             h = blcoc.Handle.from_csr(pr.A)
             h.set_option("graph", graph)
+            h.set_option("graph_conditional", graph)
             B = to_dev(torch, pr.B)
             X = torch.zeros_like(B)
             st = h.solve(B, X, method=method, tol=1e-10, maxit=30, check=False)
