@@ -399,8 +399,7 @@ def run_batched_variant(args):
     """64 independent 2D Helmholtz systems (grid side 64-512, k 5-30, damping 0.02-0.1,
     p in {1, 2, 4, 8, 16}; 5.87M rows in total), bl_cocr_rq to 1e-10: 64 separate solves,
     the CUDA-graph batch, the same batch with the tensor-core updates and explicit U per
-    system (each also with the QR fallback as a conditional graph node, option
-    graph_conditional), and the persistent kernel.  Host wall time around each call (each blocks
+    system, and the persistent kernel.  Host wall time around each call (each blocks
     until its batch is done)."""
     import torch
     from paper_1601_05362_gb300 import blcoc, problems as P
@@ -437,10 +436,8 @@ def run_batched_variant(args):
 
     run("separate_fp64", separate)
     run("graph_fp64", batched(False))
-    run("graph_fp64_conditional_fallback", batched(False), cond=1)
     if args.method == "cocr_rq":
         run("graph_fp64_tc_explicit_U", batched(False), tc=1, ue=1)
-        run("graph_fp64_tc_explicit_U_conditional_fallback", batched(False), tc=1, ue=1, cond=1)
     run("persistent_fp64", batched(True))
     for h in hs:
         h.close()
