@@ -479,12 +479,45 @@ __device__ __forceinline__ double oz_recombine(const float (&acc)[OZ_NLEV][4], i
   return oz_value<32>(acc, o, (max(ebr, 1) - 1022) + (max(ebc, 1) - 1022));
 }
 
+// largest biased exponent of real column m (< 2PP) of [Yr | Yi] over the chunk's rows, Y
+// read from global memory (Yg = the chunk's first row of a row-major n x p block, `rows`
+// of them inside n); lane m returns it (other lanes 0)
+template <int PP>
+__device__ __forceinline__ int oz_global_colexp(const double2* __restrict__ Yg, int rows, int p, int lane) {
+  int eb = 0;
+  const int kc = lane % PP;
+  if (lane < 2 * PP && kc < p) {
+    const bool im = lane >= PP;
+    for (int r = 0; r < rows; ++r) {
+      const double2 v = __ldg(Yg + (int64_t)r * p + kc);
+      eb = max(eb, oz_bexp(im ? v.y : v.x));
+    }
+  }
+  return eb;
+}
+
 // sums[tile][o][lane] += P of this chunk (Y, Z: swizzled [k][32] tiles; SAME: Z is Y).
-template <int PP, bool SAME>
-__device__ __forceinline__ void oz_gram_add(double* sums, const double2* Y, const double2* Z, int p, int lane) {
+// YG: Y is read from global memory instead (Yg, `rows` rows inside n, the rest zero).
+template <int PP, bool SAME, bool YG = false>
+__device__ __forceinline__ void oz_gram_add(double* sums, const double2* Y, const double2* Z, int p, int lane,
+                                            const double2* __restrict__ Yg = nullptr, int rows = 0) {
   using G = OzGramGeo<PP>;
   static_assert(PP == 8 || PP == 16, "exact-slice Grams are built for p <= 16");
-  const int ey = oz_tile_colexp<PP>(Y, p, lane);
+  static_assert(!(SAME && YG), "a self-Gram reads its one operand from the tile");
+  // entry (r, m) of Y' = [Yr | Yi]
+  auto yval = [&](int r, int m) -> double {
+    if constexpr (YG) {
+      const int kc = m % PP;
+      if (kc >= p || r >= rows) return 0.0;
+      const double2 v = __ldg(Yg + (int64_t)r * p + kc);
+      return m >= PP ? v.y : v.x;
+    } else {
+      return oz_tile_val<PP>(Y, p, r, m);
+    }
+  };
+  int ey;
+  if constexpr (YG) ey = oz_global_colexp<PP>(Yg, rows, p, lane);
+  else ey = oz_tile_colexp<PP>(Y, p, lane);
   const int ez = SAME ? ey : oz_tile_colexp<PP>(Z, p, lane);
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll
@@ -500,7 +533,7 @@ __device__ __forceinline__ void oz_gram_add(double* sums, const double2* Y, cons
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int r = 16 * ks + 2 * q + (c & 1) + 8 * (c >> 1);
-        const double va = oz_tile_val<PP>(Y, p, r, ma), vb = oz_tile_val<PP>(Y, p, r, mb);
+        const double va = yval(r, ma), vb = yval(r, mb);
         F[2 * c] = oz_fixed(va, eba);
         sg[2 * c] = (__double_as_longlong(va) < 0) ? 1u : 0u;
         F[2 * c + 1] = oz_fixed(vb, ebb);

@@ -829,8 +829,10 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   BLCOC_PROLOGUE(C)
   using G = Geo<PP, S>;
   constexpr bool M3A = m3_apply<PP, S, OZ>();
-  // W for the Gram read from global memory (FP64 and tensor-core variants at p = 32)
-  constexpr bool OT = one_tile<PP, S, OZ>() || tc_one_tile<PP, OZ>();
+  // W for the Gram read from global memory: the FP64 SpMM at p = 32 and every tensor-core
+  // SpMM (at p <= 16 its W^T Y slices are cut from global memory, so that the tile and the
+  // per-warp Gram sums allow 3 CTAs per SM instead of 2)
+  constexpr bool OT = one_tile<PP, S, OZ>() || OZ;
   C* T_s = smem;
   C* tiles = smem + ((M3A || OZ) ? 0 : mats_off<PP, S>(1));   // the tensor-core apply reads slices
   C* tY = tiles + warp * (OT ? 1 : 2) * G::TILE;
@@ -844,7 +846,7 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
   GramAcc<G::NTRI, S> g;
   g.init(G_SYM, p, lane);
   constexpr bool OZG = oz_gram<PP, OZ>();
-  double* zsums = reinterpret_cast<double*>(tiles + NWARP * 2 * G::TILE);   // tensor-core Gram sums
+  double* zsums = reinterpret_cast<double*>(tiles + NWARP * (OT ? 1 : 2) * G::TILE);   // tensor-core Gram sums
   if constexpr (OZG) {
     for (int i = lane; i < OzGramGeo<PP>::ACC; i += 32) zsums[warp * OzGramGeo<PP>::ACC + i] = 0.0;
   }
@@ -855,8 +857,11 @@ __device__ __forceinline__ void d_spmm_gram(const PassArgs& a, const int vblk, c
     if (!OT && !(a.flag & F_UEXPL)) load_tile<PP>(tW, blk<C>(a.W), r0, n, p, lane);   // Y^T Y needs no W
     __syncwarp();
     if constexpr (OZG) {
-      if (a.flag & F_UEXPL) oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tY, tY, p, lane);
-      else oz_gram_add<PP, false>(zsums + warp * OzGramGeo<PP>::ACC, tW, tY, p, lane);
+      if (a.flag & F_UEXPL)
+        oz_gram_add<PP, true>(zsums + warp * OzGramGeo<PP>::ACC, tY, tY, p, lane);
+      else
+        oz_gram_add<PP, false, true>(zsums + warp * OzGramGeo<PP>::ACC, nullptr, tY, p, lane, a.W + r0 * p,
+                                     (int)min((int64_t)CHUNK, n - r0));
     } else if constexpr (OT) {
       if (a.flag & F_UEXPL) g.template add<false>(tY, tY, lane);
       else g.template add_g<false>(a.W + r0 * p, (int)min((int64_t)CHUNK, n - r0), p, tY, lane);
@@ -1447,8 +1452,9 @@ constexpr size_t pass_smem(int kind) {
   // no staged factors: three-product applies, the bl_cocg_rq tensor-core passes and the
   // tensor-core SpMM (their applies read slice fragments)
   const bool m3 = (m3_apply<PP, S>() && !oz_kind) || oz_cocg || (OZ && kind == K_SPMM_GRAM);
-  const bool ot = (one_tile<PP, S, OZ>() || tc_one_tile<PP, OZ>()) &&
-                  (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C);
+  const bool ot = ((one_tile<PP, S, OZ>() || tc_one_tile<PP, OZ>()) &&
+                   (kind == K_SPMM_GRAM || kind == K_COCR_A || kind == K_COCR_C)) ||
+                  (OZ && kind == K_SPMM_GRAM);
   const int nt = (kind == K_QR2 && qr2_m3<PP, S>()) ? 2 : ((oz_cocg ? 2 : ntiles[kind]) / (ot ? 2 : 1));
   const size_t mats =
       m3 ? 0 : (size_t)(kind == K_COCR_C ? passC_mats_elems<PP, S>() : mats_off<PP, S>(nmats[kind])) * esz;
